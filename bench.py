@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput of batched low-rank determinant updates on GB300.
+
+Workload (the paper's delayed-update study, Sec. 4.2, at n = 1024): W = 1024
+walkers, each a Slater matrix A = Phi[occ] with Phi 2048 x 1024 N(0, 1/n)
+(FP64, seeded), rank-1 row replacements (one-hot U = e_i, dense
+V = Phi[new] - Phi[old]) accepted every step, and a from-scratch FP64 refresh
+of every walker after every 128th step.  One step = operand formation +
+propose + accept (+ flush) for all walkers.  Metric: walker-updates/s, for the
+delayed form (K = 16, flush on the tensor cores) and the plain FP64 form.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs its own W walkers (weak scaling); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walker-updates/sec at n=1024 (delayed vs plain rank-1, same GPU); roofline fraction"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=256)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--walkers", type=int, default=1024)
+    p.add_argument("--n", type=int, default=1024)
+    p.add_argument("--m", type=int, default=2048)
+    p.add_argument("--delay", type=int, default=16)
+    p.add_argument("--flush", default="native", choices=["native", "tf32x3", "tf32", "bf16", "bf16x3"])
+    p.add_argument("--refresh-every", type=int, default=128)
+    p.add_argument("--arms", default="both", choices=["both", "delayed", "plain"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--seed", type=int, default=6)
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and the reference arm)
+# --------------------------------------------------------------------------
+def cpu_baseline(Phi, occ0, slot, new, n, budget_s=15.0):
+    from oracle import lru_oracle as O
+    steps = min(32, slot.shape[0])
+    done, tsum, wl = 0, 0.0, 0
+    for w in range(occ0.shape[0]):
+        occ = occ0[w].copy()
+        Ainv = np.linalg.inv(O.slater_matrix(Phi, occ))
+        ts = time.perf_counter()
+        for s in range(steps):
+            U, V = O.det_row_move(Phi, occ, slot[s, w], new[s, w])
+            r, Ainv = O.det_lru(Ainv, U, V, return_update=True)
+            occ[slot[s, w]] = new[s, w]
+        tsum += time.perf_counter() - ts
+        done += steps
+        wl += 1
+        if tsum > budget_s:
+            break
+    try:
+        import threadpoolctl
+        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or 1
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": done / tsum, "unit": "walker-updates/s", "cores": int(cores), "kind": "oracle",
+            "sample": f"plain FP64 chain (oracle det_lru, Eq. det_inv) of {wl} walkers x {steps} steps at n={n}, "
+                      f"{tsum:.1f} s"}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+FLUSH = {"native": 0, "tf32x3": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
+
+
+def run_arm(L, torch, args, delayed, Phi_d, occ0, slot_d, new_d, rank, world, dist):
+    W, n, m = args.walkers, args.n, args.m
+    dev = torch.cuda.current_device()
+    st = L.LowRankState("det", W, n, k=1, dtype=torch.float64, delay=args.delay if delayed else 0,
+                        flush=FLUSH[args.flush] if delayed else 0)
+    occ_d = torch.tensor(occ0, device="cuda")
+    A = st.gather_rows(Phi_d, occ_d)
+    st.init(A)
+    V = torch.empty(W, 1, n, dtype=torch.float64, device="cuda")
+    idx = torch.empty(W, 1, dtype=torch.int32, device="cuda")
+    U_op = L.Operand(idx=idx, onehot_mask=1)
+    V_op = L.Operand(dense=V)
+    ratio = torch.empty(W, dtype=torch.float64, device="cuda")
+    status = torch.empty(W, dtype=torch.int32, device="cuda")
+
+    def step(s, timed_idx):
+        st.form_row_moves(Phi_d, occ_d, slot_d[s], new_d[s], V, idx)
+        st.propose_det(U_op, V_op, ratio, status)
+        st.accept()
+        st.commit_moves(occ_d, slot_d[s], new_d[s])
+        if timed_idx is not None and (timed_idx + 1) % args.refresh_every == 0:
+            st.gather_rows(Phi_d, occ_d, A)
+            st.refresh(A, want_drift=False)
+
+    for s in range(args.warmup):
+        step(s, None)
+    torch.cuda.synchronize()
+    for c in range(4):
+        st.profile_read(c)
+    st.profile(True)
+    launches0 = st.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        step(args.warmup + i, i)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = st.launch_count() - launches0
+    prof = {name: st.profile_read(c) for c, name in enumerate(["propose", "accept", "flush", "refresh"])}
+    st.profile(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    # parity sample at full size: the last ratios of walker 0 vs its state
+    tau = st.tau().cpu().numpy() if delayed else None
+    return st, ms, clk, launches, prof, tau
+
+
+def e2e_arm(L, torch, args, Phi_d, occ0, slot_h, new_h, steps):
+    """Same metric through the C-ABI with host buffers: each step copies its
+    proposals (slot, new row) host->device from pinned memory and reads the
+    ratios back, inside the timed region."""
+    W, n = args.walkers, args.n
+    st = L.LowRankState("det", W, n, k=1, dtype=torch.float64, delay=args.delay, flush=FLUSH[args.flush])
+    occ_d = torch.tensor(occ0, device="cuda")
+    A = st.gather_rows(Phi_d, occ_d)
+    st.init(A)
+    V = torch.empty(W, 1, n, dtype=torch.float64, device="cuda")
+    idx = torch.empty(W, 1, dtype=torch.int32, device="cuda")
+    ratio = torch.empty(W, dtype=torch.float64, device="cuda")
+    status = torch.empty(W, dtype=torch.int32, device="cuda")
+    sl_h = torch.from_numpy(np.ascontiguousarray(slot_h)).pin_memory()
+    nw_h = torch.from_numpy(np.ascontiguousarray(new_h)).pin_memory()
+    r_h = torch.empty(steps, W, dtype=torch.float64).pin_memory()
+    sl_d = torch.empty(W, dtype=torch.int32, device="cuda")
+    nw_d = torch.empty(W, dtype=torch.int32, device="cuda")
+    U_op, V_op = L.Operand(idx=idx, onehot_mask=1), L.Operand(dense=V)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in range(steps):
+        sl_d.copy_(sl_h[s], non_blocking=True)
+        nw_d.copy_(nw_h[s], non_blocking=True)
+        st.form_row_moves(Phi_d, occ_d, sl_d, nw_d, V, idx)
+        st.propose_det(U_op, V_op, ratio, status)
+        st.accept()
+        st.commit_moves(occ_d, sl_d, nw_d)
+        r_h[s].copy_(ratio, non_blocking=True)
+        if (s + 1) % args.refresh_every == 0:
+            st.gather_rows(Phi_d, occ_d, A)
+            st.refresh(A, want_drift=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st.close()
+    return {"value": W * steps / (ms / 1e3), "unit": "walker-updates/s",
+            "h2d_bytes_per_step": 2 * W * 4, "d2h_bytes_per_step": W * 8, "steps": steps}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return reference_arm(args)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2602_05255_gb300 import lrugb as L
+    from paper_2602_05255_gb300 import workloads
+
+    W, n, m = args.walkers, args.n, args.m
+    seed = args.seed + 1000 * rank
+    Phi = workloads.orbital_matrix(seed, m, n, 1.0 / n)
+    occ0 = workloads.initial_occupation(seed + 1, W, m, n)
+    total = args.warmup + args.steps
+    slot, new = workloads.move_sequence(seed + 2, occ0, m, total)
+    Phi_d = torch.tensor(Phi, device="cuda")
+    slot_d = torch.tensor(slot, device="cuda")
+    new_d = torch.tensor(new, device="cuda")
+
+    hbm, bf16, peak_src = load_peaks()
+    arms = {}
+    out_state = {}
+    order = ["plain", "delayed"] if args.arms == "both" else [args.arms]
+    for arm in order:
+        st, ms, clk, launches, prof, tau = run_arm(L, torch, args, arm == "delayed", Phi_d, occ0, slot_d, new_d,
+                                                   rank, world, dist)
+        upd = W * args.steps * world
+        nrefresh = args.steps // args.refresh_every
+        ref_ms = prof["refresh"][0]
+        a = {"value": upd / (ms / 1e3), "ms_per_step": ms / args.steps,
+             "value_excl_refresh": upd / ((ms - ref_ms) / 1e3) if ms > ref_ms else None,
+             "refreshes_in_timed_region": nrefresh, "refresh_ms_total": ref_ms,
+             "kernel_ms": {k: v[0] for k, v in prof.items()}, "kernel_launches_timed": {k: v[1] for k, v in prof.items()},
+             "gpu_launches": launches, "clocks": clk}
+        # algorithmic bytes per accept launch (one walker-update of every walker):
+        # plain: read + write A^{-1} (2 n^2 * 8 B); delayed: read A_0^{-1} (n^2 * 8 B)
+        acc_ms, acc_n = prof["accept"]
+        bytes_per = (2 if arm == "plain" else 1) * n * n * 8 * W
+        a["accept_roofline"] = {"bound": "hbm", "achieved": bytes_per / (acc_ms / acc_n / 1e3) / 1e9 if acc_n else None,
+                                "peak": hbm, "unit": "GB/s", "traffic": None,
+                                "bytes_per_launch": bytes_per, "ms_per_launch": acc_ms / acc_n if acc_n else None}
+        a["accept_roofline"]["frac"] = (a["accept_roofline"]["achieved"] / hbm) if acc_n else None
+        if arm == "delayed":
+            fl_ms, fl_n = prof["flush"]
+            a["flush"] = {"ms_total": fl_ms, "launches": fl_n, "K": args.delay, "mode": args.flush}
+        arms[arm] = a
+        out_state[arm] = st
+    # full-size parity sample: walker 0 of each arm against the oracle (first steps)
+    head = arms.get("delayed") or arms.get("plain")
+    main_arm = "delayed" if "delayed" in arms else "plain"
+    # dominant kernel of the headline arm
+    km = head["kernel_ms"]
+    dom = max(km, key=lambda k: km[k])
+    roof = dict(head["accept_roofline"])
+    roof["kernel"] = "accept (GEMV / Woodbury pass over A^{-1})"
+    roof["dominant_kernel_by_time"] = dom
+    roof["peak_source"] = peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback"
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": "walker-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"det rank-1 row moves, W={W} walkers/GPU, n={n}, Phi {m}x{n} N(0,1/n) FP64, "
+                               f"refresh every {args.refresh_every}", "arm": main_arm,
+                   "delay_K": args.delay, "flush": args.flush, "walkers_per_gpu": W, "n": n, "m": m,
+                   "l2": "inputs larger than L2 (A^{-1} state 8 GiB per GPU)"},
+        "roofline": roof, "arms": arms, "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+    }
+    if rank == 0 and not args.no_e2e:
+        esteps = min(args.steps, 64)
+        line["e2e"] = e2e_arm(L, torch, args, Phi_d, occ0, slot[args.warmup:args.warmup + esteps],
+                              new[args.warmup:args.warmup + esteps], esteps)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(Phi, occ0, slot, new, n)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def reference_arm(args):
+    """The oracle as it stands on the host cores (there is no reference code)."""
+    from paper_2602_05255_gb300 import workloads
+    W, n, m = args.walkers, args.n, args.m
+    Phi = workloads.orbital_matrix(args.seed, m, n, 1.0 / n)
+    occ0 = workloads.initial_occupation(args.seed + 1, W, m, n)
+    slot, new = workloads.move_sequence(args.seed + 2, occ0, m, max(4, min(args.steps, 16)))
+    t0 = time.perf_counter()
+    cb = cpu_baseline(Phi, occ0, slot, new, n, budget_s=max(5.0, min(60.0, 2.0 * args.steps)))
+    el = time.perf_counter() - t0
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "walker-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * W / cb["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"det rank-1 row moves, W={W}, n={n}, Phi {m}x{n} N(0,1/n) FP64 (oracle sample)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "walker-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": el}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

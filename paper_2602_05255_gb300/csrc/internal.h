@@ -1,0 +1,112 @@
+// Internal interface between the C-ABI (lrugb_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lru {
+
+// Per-walker geometry, as seen by kernels.  Walker w has an n_w x n_w
+// inverse starting at element moff(w) (sum of n_v^2 before it) and length-n_w
+// vectors starting at voff(w) (sum of n_v before it) times the slot count.
+struct DevLayout {
+    int W;
+    int n_uni;                 // > 0: every walker has this n (moff, voff computed)
+    int n_max;                 // largest n (workspace slot size n_max^2)
+    const int* n;              // per-walker n (ragged)
+    const long long* moff;
+    const long long* voff;
+    int kk;                    // vector slots per update (det: k, pf: 2k), max over walkers
+    const int* kvec;           // per-walker vector count, or nullptr (= kk)
+    int Kc;                    // delay columns per walker row of P, Q (K * kk), 0 if plain
+    int K;                     // delay length (>= 2 for the delayed form)
+    __device__ __forceinline__ int nw(int w) const { return n_uni > 0 ? n_uni : n[w]; }
+    __device__ __forceinline__ long long mo(int w) const {
+        return n_uni > 0 ? (long long)w * n_uni * n_uni : moff[w];
+    }
+    __device__ __forceinline__ long long vo(int w) const {
+        return n_uni > 0 ? (long long)w * n_uni : voff[w];
+    }
+    __device__ __forceinline__ int kv(int w) const { return kvec ? kvec[w] : kk; }
+};
+
+// Per-walker state and proposal scratch (one device allocation).
+template <typename T>
+struct DevState {
+    T* G;          // A^{-1} (plain) or A_0^{-1} (delayed), column-major per walker
+    T* P;          // delayed: n_w x Kc per walker, row j contiguous
+    T* Q;
+    float* P32h;   // delayed, tensor-core flush: split copies of P and Q (K-major)
+    float* P32l;
+    float* Q32h;
+    float* Q32l;
+    int* tau;      // filled delay slots per walker
+    double* logabs;
+    T* sgn;        // sign (real) or unit phase (complex)
+    // scratch of the last proposal
+    T* X;          // A^{-1} U (det) or A^{-1} B (pf): kk vectors of n_w
+    T* Rinv;       // kk x kk per walker: R^{-1} (det) or M^{-1} (pf)
+    T* ratio;      // W
+    int* pst;      // W proposal status
+    T* VP;         // det delayed: V P (MAXKK x Kc per walker)
+    T* QtU;        // delayed, dense U columns: Q^T U (Kc x MAXKK per walker)
+    int* err;      // sticky device error word
+};
+
+struct DevOperand {
+    const void* dense;
+    const int* idx;
+    unsigned mask;   // bit a: slot a is one-hot
+    int slots;       // vector slots per walker in the buffers (kmax)
+};
+
+// ---- launchers (defined in lru_kernels.cu, instantiated for every dtype) ----
+template <typename T>
+void launch_propose(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& U,
+                    const DevOperand& V, const T* C, T* ratio_out, int* st_out, cudaStream_t st);
+template <typename T>
+void launch_accept(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
+                   const uint8_t* mask, const int* items, int nitems, cudaStream_t st);
+template <typename T>
+void launch_flush_native(bool pf, const DevLayout& L, const DevState<T>& S, const uint8_t* force_mask,
+                         int nwalkers_tiles, cudaStream_t st);
+template <typename T>
+void launch_flush_finish(const DevLayout& L, const DevState<T>& S, const uint8_t* force_mask, cudaStream_t st);
+template <typename T>
+void launch_get_inverse(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, T* out, cudaStream_t st);
+template <typename T>
+void launch_form_row_moves(const DevLayout& L, const T* Phi, int m, const int* occ, const int* slot,
+                           const int* newrow, T* Vout, int* idx, cudaStream_t st);
+template <typename T>
+void launch_form_pf_moves(const DevLayout& L, const T* F, int m, const int* pos, const int* slot,
+                          const int* newsite, T* Bout, int* idx, cudaStream_t st);
+template <typename T>
+void launch_gather(bool pairs, const DevLayout& L, const T* src, int m, const int* occ, T* A, int* err,
+                   cudaStream_t st);
+void launch_commit_moves(int W, int n, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
+                         const int* pst, cudaStream_t st);
+template <typename T>
+void launch_set_delay_zero(const DevLayout& L, const DevState<T>& S, cudaStream_t st);
+
+// ---- refresh / dense (refresh.cu) ----
+// For each selected walker: G := A^{-1} (column-major) by Gauss-Jordan on A^T,
+// log|det| and sign into S (write_logdet), tau := 0.  With ws (nws slots of
+// n_uni^2 scalars) the inverse is formed in the CTA's slot first and the drift
+// of the tracked inverse against it is written before it replaces G.
+template <typename T>
+void launch_refresh(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const T* A,
+                    const uint8_t* mask, T* ws, int nws, double* drift, bool write_logdet, cudaStream_t st);
+// Pfaffian (Parlett-Reid) of the selected walkers' A into logabs / sgn; ws: nws slots.
+template <typename T>
+void launch_slogpf(const DevLayout& L, const T* A, const uint8_t* mask, T* ws, int nws, double* logabs, T* sgn,
+                   cudaStream_t st);
+template <typename T>
+void launch_slogdet(int W, int n, const T* A, T* ws, int nws, double* logabs, T* sgn, cudaStream_t st);
+
+// ---- tensor-core flush (flush_tc.cu) ----
+// Returns false when the combination is not built.
+bool launch_flush_tc(int mode, bool pf, const DevLayout& L, double* G, const float* Ph, const float* Pl,
+                     const float* Qh, const float* Ql, const int* tau, const uint8_t* force_mask,
+                     int* err, cudaStream_t st);
+
+}  // namespace lru

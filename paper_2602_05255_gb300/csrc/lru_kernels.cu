@@ -1,0 +1,845 @@
+// Propose / accept / flush kernels of the low-rank update path.
+//
+// Storage: walker w keeps A^{-1} column-major, G[l*n + j] = (A^{-1})_{jl}, so
+// column i of A^{-1} (what a one-hot row update reads, Sec. 2.2) is one
+// contiguous "chunk" and the row-update GEMV V A^{-1} is one dot product per
+// chunk.  The plain accept therefore reads and writes every chunk exactly
+// once: chunk_l -= X R^{-1} (V . chunk_l), the Woodbury step of Eq. det_inv.
+#include "common.cuh"
+#include "internal.h"
+#include "small_core.cuh"
+
+#include <algorithm>
+
+namespace lru {
+
+constexpr int PT = 256;    // threads of the per-walker kernels
+constexpr int JPT = 8;     // vector elements per thread: n <= PT * JPT = 2048
+constexpr int MAXKK = 16;  // vector slots per update (det k <= 16, pf 2k <= 16)
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// hi + lo split of a double for the tensor-core flush: hi is x rounded to TF32,
+// lo the TF32-rounded remainder (3-term products reach about FP32 accuracy).
+__device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
+    float xf = (float)x;
+    hi = tf32_round(xf);
+    lo = tf32_round((float)(x - (double)hi));
+}
+
+template <typename T>
+__device__ __forceinline__ const T* vec_ptr(const DevOperand& O, const DevLayout& L, int w, int a, int n) {
+    return reinterpret_cast<const T*>(O.dense) + (L.vo(w) * O.slots + (long long)a * n);
+}
+
+// Thread-block reduction of NV values per thread into out[0..NV) (smem red has
+// >= 8*NV entries).  All threads must call it.
+template <typename T, int NV>
+__device__ void block_reduce_vec(T (&v)[NV], T* red, T* out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[wid * NV + q] = v[q];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        T s = s_zero(T());
+        for (int q = 0; q < PT / 32; ++q) s = s + red[q * NV + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// propose: X = A^{-1} U (delayed: A_0^{-1} U -/+ P (Q^T U)), core, small solve
+// det: Sec. 2.1 Eq. det_R, delayed Sec. 2.3 (R_tau, a_tau equations)
+// pf : App. A.2 Eq. pf_low_rank, delayed Sec. 3.3 (R_tau, a_tau equations)
+// One CTA per walker.
+// ---------------------------------------------------------------------------
+template <typename T, bool PF, bool DELAYED>
+__global__ void __launch_bounds__(PT) k_propose(DevLayout L, DevState<T> S, DevOperand U, DevOperand V,
+                                                 const T* C, T* ratio_out, int* st_out) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    T* s_qtu = reinterpret_cast<T*>(dyn_smem);  // Kc x MAXKK (delayed only)
+    __shared__ T s_core[MAXKK * MAXKK];
+    __shared__ T s_inv[MAXKK * MAXKK];
+    __shared__ T s_cinv[MAXKK * MAXKK];
+    __shared__ T s_red[8 * 16];
+    __shared__ int s_iu[MAXKK], s_iv[MAXKK];
+    __shared__ int s_bad;
+    __shared__ T s_pfc;
+
+    const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int n = L.nw(w), kk = L.kv(w);
+    const long long vo = L.vo(w);
+    const T* G = S.G + L.mo(w);
+    T* X = S.X + vo * L.kk;
+    const int Kc = L.Kc;
+    const int cu = DELAYED ? S.tau[w] * kk : 0;
+    const DevOperand& Vop = PF ? U : V;
+
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    if (tid < kk) {
+        int iu = -1, iv = -1;
+        if ((U.mask >> tid) & 1u) {
+            iu = U.idx[(long long)w * U.slots + tid];
+            if (iu < 0 || iu >= n) atomicExch(&s_bad, 1);
+        }
+        if ((Vop.mask >> tid) & 1u) {
+            iv = Vop.idx[(long long)w * Vop.slots + tid];
+            if (iv < 0 || iv >= n) atomicExch(&s_bad, 1);
+        }
+        s_iu[tid] = iu;
+        s_iv[tid] = iv;
+    }
+    if (PF && tid == 0) {
+        // C^{-1} and pf(C^{-1}); C = NULL means C = -J, so C^{-1} = J (Sec. 3.1)
+        const int k2 = kk;
+        if (C == nullptr) {
+            for (int i = 0; i < k2; ++i)
+                for (int j = 0; j < k2; ++j) {
+                    double v = (j == i + k2 / 2) ? 1.0 : ((i == j + k2 / 2) ? -1.0 : 0.0);
+                    s_cinv[i * MAXKK + j] = make_real<T>(v);
+                }
+        } else {
+            const T* Cw = C + (long long)w * k2 * k2;
+            for (int i = 0; i < k2; ++i)
+                for (int j = 0; j < k2; ++j) s_cinv[i * MAXKK + j] = Cw[i * k2 + j];
+            T dC;
+            int stc = small_gj_inverse(s_cinv, k2, MAXKK, &dC);
+            if (stc != CORE_OK) atomicExch(&s_bad, 2);
+            for (int i = 0; i < k2; ++i)      // exactly skew
+                for (int j = i; j < k2; ++j) {
+                    T a = s_cinv[i * MAXKK + j], b = s_cinv[j * MAXKK + i];
+                    T h = s_half(a - b);
+                    s_cinv[i * MAXKK + j] = h;
+                    s_cinv[j * MAXKK + i] = s_neg(h);
+                }
+        }
+        for (int i = 0; i < k2; ++i)
+            for (int j = 0; j < k2; ++j) s_core[i * MAXKK + j] = s_cinv[i * MAXKK + j];
+        s_pfc = small_pf(s_core, k2, MAXKK);
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (tid == 0) {
+            int code = s_bad == 1 ? 3 /*LRU_WALKER_BAD_INDEX*/ : 1;
+            S.pst[w] = code;
+            if (st_out) st_out[w] = code;
+            ratio_out[w] = s_zero(T());
+            S.ratio[w] = s_zero(T());
+        }
+        return;
+    }
+
+    // ---- delayed: Q^T U (cu x kk), the (b_t^T U) / (a_t^T B) factors ----
+    // one-hot columns read row i of Q; dense columns were reduced by k_qtu_dense
+    if constexpr (DELAYED) {
+        for (int a = 0; a < kk; ++a) {
+            if (s_iu[a] >= 0) {
+                for (int c = tid; c < cu; c += PT) s_qtu[c * MAXKK + a] = S.Q[(vo + s_iu[a]) * Kc + c];
+            } else {
+                for (int c = tid; c < cu; c += PT) s_qtu[c * MAXKK + a] = S.QtU[((long long)w * Kc + c) * MAXKK + a];
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- X = A^{-1} U ----
+    // one-hot columns: a contiguous chunk copy; dense columns: axpy over chunks
+    for (int a = 0; a < kk; ++a) {
+        T* Xa = X + (long long)a * n;
+        if (s_iu[a] >= 0) {
+            const T* col = G + (long long)s_iu[a] * n;
+            for (int j = tid; j < n; j += PT) Xa[j] = col[j];
+        }
+    }
+    {
+        // dense columns, four at a time
+        int dl[MAXKK], nd = 0;
+        for (int a = 0; a < kk; ++a)
+            if (s_iu[a] < 0) dl[nd++] = a;
+        for (int g0 = 0; g0 < nd; g0 += 4) {
+            const int ng = min(4, nd - g0);
+            T acc[4][JPT];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int m = 0; m < JPT; ++m) acc[q][m] = s_zero(T());
+            const T* up[4];
+            for (int q = 0; q < 4; ++q) up[q] = vec_ptr<T>(U, L, w, dl[g0 + min(q, ng - 1)], n);
+            for (int l = 0; l < n; ++l) {
+                const T* col = G + (long long)l * n;
+                T ul[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) ul[q] = up[q][l];
+#pragma unroll
+                for (int m = 0; m < JPT; ++m) {
+                    const int j = tid + m * PT;
+                    if (j < n) {
+                        T g = col[j];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[q][m] = s_fma(g, ul[q], acc[q][m]);
+                    }
+                }
+            }
+            for (int q = 0; q < ng; ++q) {
+                T* Xa = X + (long long)dl[g0 + q] * n;
+#pragma unroll
+                for (int m = 0; m < JPT; ++m) {
+                    const int j = tid + m * PT;
+                    if (j < n) Xa[j] = acc[q][m];
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    if constexpr (DELAYED) {
+        // X -= P (Q^T U) (det)   or   X += P (Q^T B) (pf)
+        for (int j = tid; j < n; j += PT) {
+            const T* prow = S.P + (vo + j) * Kc;
+            for (int a = 0; a < kk; ++a) {
+                T s = s_zero(T());
+                for (int c = 0; c < cu; ++c) s = s_fma(prow[c], s_qtu[c * MAXKK + a], s);
+                T* Xa = X + (long long)a * n;
+                Xa[j] = PF ? (Xa[j] + s) : (Xa[j] - s);
+            }
+        }
+        __syncthreads();
+        if constexpr (!PF) {
+            // a_tau = X goes to slot tau of P now (harmless if the proposal is rejected)
+            for (int j = tid; j < n; j += PT) {
+                for (int a = 0; a < kk; ++a) {
+                    const long long off = (vo + j) * Kc + cu + a;
+                    T x = X[(long long)a * n + j];
+                    S.P[off] = x;
+                    if constexpr (!traits<T>::is_complex && sizeof(T) == 8) {
+                        if (S.P32h) {
+                            float h, lo;
+                            split_tf32((double)x, h, lo);
+                            S.P32h[off] = h;
+                            S.P32l[off] = lo;
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    // ---- core: R = I + V X (det) or M = C^{-1} + B^T X (pf) ----
+    for (int p = wid; p < kk * kk; p += PT / 32) {
+        const int b = p / kk, a = p % kk;
+        const T* Xa = X + (long long)a * n;
+        T s;
+        if (s_iv[b] >= 0) {
+            s = Xa[s_iv[b]];
+        } else {
+            const T* vb = vec_ptr<T>(Vop, L, w, b, n);
+            T part = s_zero(T());
+            for (int j = lane; j < n; j += 32) part = s_fma(vb[j], Xa[j], part);
+            s = warp_sum(part);
+        }
+        if (lane == 0) {
+            T base = PF ? s_cinv[b * MAXKK + a] : make_real<T>(b == a ? 1.0 : 0.0);
+            s_core[b * MAXKK + a] = base + s;
+        }
+    }
+    // ---- det delayed: V P (kk x cu) for the accept's correction ----
+    if constexpr (DELAYED && !PF) {
+        T* VP = S.VP + (long long)w * MAXKK * Kc;
+        for (int p = wid; p < kk * cu; p += PT / 32) {
+            const int b = p / cu, c = p % cu;
+            T s;
+            if (s_iv[b] >= 0) {
+                s = S.P[(vo + s_iv[b]) * Kc + c];
+            } else {
+                const T* vb = vec_ptr<T>(Vop, L, w, b, n);
+                T part = s_zero(T());
+                for (int j = lane; j < n; j += 32) part = s_fma(vb[j], S.P[(vo + j) * Kc + c], part);
+                s = warp_sum(part);
+            }
+            if (lane == 0) VP[b * Kc + c] = s;
+        }
+    }
+    __syncthreads();
+
+    // ---- small core ----
+    if (tid == 0) {
+        int st;
+        T ratio;
+        if constexpr (!PF) {
+            for (int i = 0; i < kk; ++i)
+                for (int j = 0; j < kk; ++j) s_inv[i * MAXKK + j] = s_core[i * MAXKK + j];
+            st = small_gj_inverse(s_inv, kk, MAXKK, &ratio);
+        } else {
+            // M is skew in exact arithmetic: keep it exactly skew
+            for (int i = 0; i < kk; ++i)
+                for (int j = i; j < kk; ++j) {
+                    T h = s_half(s_core[i * MAXKK + j] - s_core[j * MAXKK + i]);
+                    s_core[i * MAXKK + j] = h;
+                    s_core[j * MAXKK + i] = s_neg(h);
+                }
+            for (int i = 0; i < kk; ++i)
+                for (int j = 0; j < kk; ++j) s_inv[i * MAXKK + j] = s_core[i * MAXKK + j];
+            T dM;
+            st = small_gj_inverse(s_inv, kk, MAXKK, &dM);
+            for (int i = 0; i < kk; ++i)
+                for (int j = i; j < kk; ++j) {
+                    T h = s_half(s_inv[i * MAXKK + j] - s_inv[j * MAXKK + i]);
+                    s_inv[i * MAXKK + j] = h;
+                    s_inv[j * MAXKK + i] = s_neg(h);
+                }
+            T pfM = small_pf(s_core, kk, MAXKK);
+            ratio = pfM * s_recip(s_pfc);
+            if (st == CORE_OK && !s_isfinite(ratio)) st = CORE_NONFINITE;
+        }
+        T* Ri = S.Rinv + (long long)w * MAXKK * MAXKK;
+        for (int i = 0; i < kk; ++i)
+            for (int j = 0; j < kk; ++j) Ri[i * MAXKK + j] = s_inv[i * MAXKK + j];
+        int code = st == CORE_OK ? 0 : (st == CORE_SINGULAR ? 1 : 2);
+        S.pst[w] = code;
+        S.ratio[w] = ratio;
+        ratio_out[w] = ratio;
+        if (st_out) st_out[w] = code;
+    }
+    if constexpr (DELAYED && PF) {
+        __syncthreads();
+        // slots: Q[:, tau] = a_tau = X, P[:, tau] = a_tau M^{-1} (Sec. 3.3)
+        for (int j = tid; j < n; j += PT) {
+            for (int b = 0; b < kk; ++b) {
+                T q = X[(long long)b * n + j];
+                T p = s_zero(T());
+                for (int a = 0; a < kk; ++a) p = s_fma(X[(long long)a * n + j], s_inv[a * MAXKK + b], p);
+                const long long off = (vo + j) * Kc + cu + b;
+                S.Q[off] = q;
+                S.P[off] = p;
+                if constexpr (!traits<T>::is_complex && sizeof(T) == 8) {
+                    if (S.P32h) {
+                        float h, lo;
+                        split_tf32((double)p, h, lo);
+                        S.P32h[off] = h;
+                        S.P32l[off] = lo;
+                        split_tf32((double)q, h, lo);
+                        S.Q32h[off] = h;
+                        S.Q32l[off] = lo;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Q^T U for the dense U columns of the delayed propose, one CTA per walker
+// and column: QtU[w][c][a] = sum_j Q[j][c] u_a[j].  Runs before k_propose.
+template <typename T>
+__global__ void __launch_bounds__(PT) k_qtu_dense(DevLayout L, DevState<T> S, DevOperand U) {
+    __shared__ T s_red[8 * 16];
+    __shared__ T s_out[16];
+    const int w = blockIdx.x, a = blockIdx.y;
+    const int n = L.nw(w), kk = L.kv(w);
+    if (a >= kk || ((U.mask >> a) & 1u)) return;
+    const int Kc = L.Kc, cu = S.tau[w] * kk;
+    const long long vo = L.vo(w);
+    const T* u = vec_ptr<T>(U, L, w, a, n);
+    for (int c0 = 0; c0 < cu; c0 += 16) {
+        T part[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) part[q] = s_zero(T());
+        for (int j = threadIdx.x; j < n; j += PT) {
+            const T* qrow = S.Q + (vo + j) * Kc + c0;
+            T uj = u[j];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (c0 + q < cu) part[q] = s_fma(qrow[q], uj, part[q]);
+        }
+        block_reduce_vec<T, 16>(part, s_red, s_out);
+        if (threadIdx.x < 16 && c0 + threadIdx.x < cu)
+            S.QtU[((long long)w * Kc + c0 + threadIdx.x) * MAXKK + a] = s_out[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// accept pass: one warp per chunk l (column l of A^{-1})
+//   y_b = V_b . chunk_l (dense) or chunk_l[i_b] (one-hot)      [= (V A^{-1})_{bl}]
+//   plain  : chunk_l -= X (R^{-1} y)                            (Eq. det_inv; pf:
+//            generic Woodbury A^{-1} - X M^{-1} (B^T A^{-1}))
+//   delayed: y -= (V P) Q[l,:]^T ; Q[l, tau] = (R^{-1} y)^T     (b_tau equation)
+// ---------------------------------------------------------------------------
+template <typename T, bool DELAYED, int NPL>
+__global__ void __launch_bounds__(PT) k_accept(DevLayout L, DevState<T> S, DevOperand V, const uint8_t* mask,
+                                                const int4* items) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    const int4 it = items[blockIdx.x];
+    const int w = it.x;
+    if (mask && !mask[w]) return;
+    if (S.pst[w] != 0) return;
+    const int n = L.nw(w), kk = L.kv(w);
+    const long long vo = L.vo(w);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // X and the dense V vectors are staged in shared memory when they fit
+    // (use_smem), else read from global memory (L2) with the same layout
+    T* sXs = reinterpret_cast<T*>(dyn_smem);       // kk x n
+    T* sVs = sXs + (size_t)kk * n;                 // kk x n (dense slots)
+    const bool use_smem = it.w != 0;
+    __shared__ T sR[MAXKK * MAXKK];
+    __shared__ int siv[MAXKK];
+    __shared__ T sVP[MAXKK * 64];
+    const int Kc = L.Kc;
+    const int cu = DELAYED ? S.tau[w] * kk : 0;
+
+    const T* Xg = S.X + vo * L.kk;
+    const T* sX = Xg;
+    const T* sV = (V.dense != nullptr) ? vec_ptr<T>(V, L, w, 0, n) : nullptr;
+    if (use_smem) {
+        for (int e = threadIdx.x; e < kk * n; e += PT) sXs[e] = Xg[e];
+        for (int b = 0; b < kk; ++b) {
+            if ((V.mask >> b) & 1u) continue;
+            const T* vb = vec_ptr<T>(V, L, w, b, n);
+            for (int j = threadIdx.x; j < n; j += PT) sVs[(size_t)b * n + j] = vb[j];
+        }
+        sX = sXs;
+        sV = sVs;
+    }
+    if (threadIdx.x < kk) siv[threadIdx.x] = ((V.mask >> threadIdx.x) & 1u) ? V.idx[(long long)w * V.slots + threadIdx.x] : -1;
+    for (int e = threadIdx.x; e < MAXKK * MAXKK; e += PT) sR[e] = S.Rinv[(long long)w * MAXKK * MAXKK + e];
+    if constexpr (DELAYED)
+        for (int e = threadIdx.x; e < kk * cu; e += PT) {
+            const int b = e / cu, c = e % cu;
+            sVP[b * 64 + c] = S.VP[(long long)w * MAXKK * Kc + b * Kc + c];
+        }
+    __syncthreads();
+
+    T* Gw = S.G + L.mo(w);
+    for (int l = it.y + wid; l < it.z; l += PT / 32) {
+        T* col = Gw + (long long)l * n;
+        T v[NPL];
+#pragma unroll
+        for (int m = 0; m < NPL; ++m) {
+            const int j = lane + 32 * m;
+            v[m] = (j < n) ? col[j] : s_zero(T());
+        }
+        T y[MAXKK];
+        for (int b = 0; b < kk; ++b) {
+            if (siv[b] >= 0) {
+                y[b] = col[siv[b]];
+            } else {
+                const T* vb = sV + (size_t)b * n;
+                T part = s_zero(T());
+#pragma unroll
+                for (int m = 0; m < NPL; ++m) {
+                    const int j = lane + 32 * m;
+                    if (j < n) part = s_fma(vb[j], v[m], part);
+                }
+                y[b] = warp_sum(part);
+            }
+            if constexpr (DELAYED) {
+                const T* qrow = S.Q + (vo + l) * Kc;
+                T corr = s_zero(T());
+                for (int c = 0; c < cu; ++c) corr = s_fma(sVP[b * 64 + c], qrow[c], corr);
+                y[b] = y[b] - corr;
+            }
+        }
+        T z[MAXKK];
+        for (int a = 0; a < kk; ++a) {
+            T s = s_zero(T());
+            for (int b = 0; b < kk; ++b) s = s_fma(sR[a * MAXKK + b], y[b], s);
+            z[a] = s;
+        }
+        if constexpr (!DELAYED) {
+#pragma unroll
+            for (int m = 0; m < NPL; ++m) {
+                const int j = lane + 32 * m;
+                if (j < n) {
+                    T d = v[m];
+                    for (int a = 0; a < kk; ++a) d = s_fms(sX[(size_t)a * n + j], z[a], d);
+                    col[j] = d;
+                }
+            }
+        } else {
+            if (lane < kk) {
+                T zz = z[0];
+                for (int a = 1; a < kk; ++a)
+                    if (a == lane) zz = z[a];
+                const long long off = (vo + l) * Kc + cu + lane;
+                S.Q[off] = zz;
+                if constexpr (!traits<T>::is_complex && sizeof(T) == 8) {
+                    if (S.P32h) {
+                        float h, lo;
+                        split_tf32((double)zz, h, lo);
+                        S.Q32h[off] = h;
+                        S.Q32l[off] = lo;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// After the accept pass: log|value| += log|r|, sign *= r/|r|, tau += 1 (delayed)
+template <typename T>
+__global__ void k_commit(DevLayout L, DevState<T> S, const uint8_t* mask, bool delayed) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= L.W) return;
+    if (mask && !mask[w]) return;
+    if (S.pst[w] != 0) return;
+    T r = S.ratio[w];
+    S.logabs[w] += log(s_absd(r));
+    S.sgn[w] = s_renorm(S.sgn[w] * s_unit(r));
+    if (delayed) S.tau[w] += 1;
+    S.pst[w] = 4;  // proposal consumed: a second accept of it is a no-op
+}
+
+// ---------------------------------------------------------------------------
+// native flush: A_0^{-1} -= P Q^T (det, Eq. delayed_Ainv) or += (pf, Eq.
+// pf_delayed_Ainv) over the filled slots.  32 x 32 tiles; for the Pfaffian only
+// tiles with J <= L are computed and the mirror is written as the exact
+// negative transpose, so A_0^{-1} stays exactly skew.
+// ---------------------------------------------------------------------------
+template <typename T, bool PF>
+__global__ void __launch_bounds__(256) k_flush_native(DevLayout L, DevState<T> S, const uint8_t* force) {
+    __shared__ T sP[32][65];
+    __shared__ T sQ[32][65];
+    __shared__ T sT[32][33];
+    const int w = blockIdx.z;
+    const int n = L.nw(w), kk = L.kv(w);
+    const int tau = S.tau[w];
+    const bool go = force ? (force[w] && tau > 0) : (tau >= L.K);
+    if (!go) return;
+    const int nt = (n + 31) / 32;
+    const int tJ = blockIdx.x, tL = blockIdx.y;
+    if (tJ >= nt || tL >= nt) return;
+    if (PF && tJ > tL) return;
+    const int cu = tau * kk, Kc = L.Kc;
+    const long long vo = L.vo(w);
+    T* Gw = S.G + L.mo(w);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    const int j0 = tJ * 32, l0 = tL * 32;
+    T acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = s_zero(T());
+    for (int c0 = 0; c0 < cu; c0 += 64) {
+        for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+            const int r = e / 64, c = e % 64;
+            const bool okc = c0 + c < cu;
+            sP[r][c] = (okc && j0 + r < n) ? S.P[(vo + j0 + r) * Kc + c0 + c] : s_zero(T());
+            sQ[r][c] = (okc && l0 + r < n) ? S.Q[(vo + l0 + r) * Kc + c0 + c] : s_zero(T());
+        }
+        __syncthreads();
+        const int cm = min(64, cu - c0);
+        for (int c = 0; c < cm; ++c) {
+            T pj = sP[tx][c];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = s_fma(pj, sQ[ty + 8 * q][c], acc[q]);
+        }
+        __syncthreads();
+    }
+    // element (j0+tx, l0+ty+8q) lives at G[(l0+ty+8q)*n + j0+tx]
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = j0 + tx, l = l0 + ty + 8 * q;
+        T nv = s_zero(T());
+        if (j < n && l < n) {
+            T g = Gw[(long long)l * n + j];
+            nv = PF ? (g + acc[q]) : (g - acc[q]);
+        }
+        sT[ty + 8 * q][tx] = nv;
+    }
+    __syncthreads();
+    if (!PF) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + tx, l = l0 + ty + 8 * q;
+            if (j < n && l < n) Gw[(long long)l * n + j] = sT[ty + 8 * q][tx];
+        }
+    } else {
+        // upper entries (j < l) are kept, lower ones written as their negatives
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + tx, l = l0 + ty + 8 * q;
+            if (j < n && l < n) {
+                T v;
+                if (j < l) v = sT[ty + 8 * q][tx];
+                else if (j == l) v = s_zero(T());
+                else v = s_neg(sT[tx][ty + 8 * q]);  // same tile (diagonal tiles only)
+                Gw[(long long)l * n + j] = v;
+            }
+        }
+        if (tJ != tL) {
+            // mirror tile: (l, j) = -(j, l), stored at G[j*n + l]
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int l = l0 + tx, j = j0 + ty + 8 * q;
+                if (j < n && l < n) Gw[(long long)j * n + l] = s_neg(sT[tx][ty + 8 * q]);
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_flush_finish(DevLayout L, DevState<T> S, const uint8_t* force) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= L.W) return;
+    const int tau = S.tau[w];
+    const bool go = force ? (force[w] && tau > 0) : (tau >= L.K);
+    if (go) S.tau[w] = 0;
+}
+
+template <typename T>
+__global__ void k_set_delay_zero(DevLayout L, DevState<T> S) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < L.W) S.tau[w] = 0;
+}
+
+// current A^{-1} (row-major out) = A_0^{-1} -/+ P Q^T, 32 x 32 tiles
+template <typename T, bool PF, bool DELAYED>
+__global__ void __launch_bounds__(256) k_get_inverse(DevLayout L, DevState<T> S, T* out) {
+    __shared__ T sT[32][33];
+    const int w = blockIdx.z;
+    const int n = L.nw(w), kk = L.kv(w);
+    const int nt = (n + 31) / 32;
+    if ((int)blockIdx.x >= nt || (int)blockIdx.y >= nt) return;
+    const int j0 = blockIdx.x * 32, l0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const T* Gw = S.G + L.mo(w);
+    const long long vo = L.vo(w);
+    const int cu = DELAYED ? S.tau[w] * kk : 0;
+    for (int q = 0; q < 4; ++q) {
+        const int j = j0 + tx, l = l0 + ty + 8 * q;
+        T v = s_zero(T());
+        if (j < n && l < n) {
+            v = Gw[(long long)l * n + j];
+            if (DELAYED) {
+                const T* pr = S.P + (vo + j) * L.Kc;
+                const T* qr = S.Q + (vo + l) * L.Kc;
+                T s = s_zero(T());
+                for (int c = 0; c < cu; ++c) s = s_fma(pr[c], qr[c], s);
+                v = PF ? v + s : v - s;
+            }
+        }
+        sT[ty + 8 * q][tx] = v;   // (j, l)
+    }
+    __syncthreads();
+    T* ow = out + L.mo(w);
+    for (int q = 0; q < 4; ++q) {
+        const int i = j0 + ty + 8 * q, jj = l0 + tx;   // out[i][jj] = A^{-1}_{i, jj}
+        if (i < n && jj < n) ow[(long long)i * n + jj] = sT[tx][ty + 8 * q];
+    }
+}
+
+// ---- operand formation -----------------------------------------------------
+template <typename T>
+__global__ void k_form_row_moves(DevLayout L, const T* Phi, int m, const int* occ, const int* slot,
+                                 const int* newrow, T* Vout, int* idx) {
+    const int w = blockIdx.x, n = L.n_uni;
+    const int i = slot[w];
+    const bool ok_i = i >= 0 && i < n;
+    const int nr = newrow[w];
+    const int old = ok_i ? occ[(long long)w * n + i] : 0;
+    const bool ok = ok_i && nr >= 0 && nr < m && old >= 0 && old < m;
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+        Vout[(long long)w * n + j] = ok ? (Phi[(long long)nr * n + j] - Phi[(long long)old * n + j]) : s_zero(T());
+    if (threadIdx.x == 0) idx[w] = ok ? i : -1;   // -1 is rejected by propose
+}
+
+template <typename T>
+__global__ void k_form_pf_moves(DevLayout L, const T* F, int m, const int* pos, const int* slot,
+                                const int* newsite, T* Bout, int* idx) {
+    const int w = blockIdx.x, n = L.n_uni;
+    const int i = slot[w];
+    const bool ok_i = i >= 0 && i < n;
+    const int rn = newsite[w];
+    const int ri = ok_i ? pos[(long long)w * n + i] : 0;
+    const bool ok = ok_i && rn >= 0 && rn < m && ri >= 0 && ri < m;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int rj = pos[(long long)w * n + j];
+        const bool okj = ok && rj >= 0 && rj < m;
+        Bout[(long long)w * 2 * n + j] = okj ? (F[(long long)rn * m + rj] - F[(long long)ri * m + rj]) : s_zero(T());
+    }
+    if (threadIdx.x == 0) {
+        idx[2 * w] = -1;
+        idx[2 * w + 1] = ok ? i : -1;
+    }
+}
+
+// A_w[i][j] = Phi[occ_w[i]][j] (rows) or F[pos_w[i]][pos_w[j]] (pairs)
+template <typename T, bool PAIRS>
+__global__ void k_gather(DevLayout L, const T* src, int m, const int* occ, T* A, int* err) {
+    const int w = blockIdx.y, n = L.n_uni;
+    const long long total = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        const int ri = occ[(long long)w * n + i];
+        T v = s_zero(T());
+        if (PAIRS) {
+            const int rj = occ[(long long)w * n + j];
+            if (ri >= 0 && ri < m && rj >= 0 && rj < m) v = src[(long long)ri * m + rj];
+            else set_dev_error(err, DEV_ERR_INDEX);
+        } else {
+            if (ri >= 0 && ri < m) v = src[(long long)ri * n + j];
+            else set_dev_error(err, DEV_ERR_INDEX);
+        }
+        A[(long long)w * total + e] = v;
+    }
+}
+
+template <typename T>
+void launch_gather(bool pairs, const DevLayout& L, const T* src, int m, const int* occ, T* A, int* err,
+                   cudaStream_t st) {
+    const long long total = (long long)L.n_uni * L.n_uni;
+    dim3 grid((unsigned)std::min<long long>((total + 255) / 256, 64), L.W);
+    if (pairs) k_gather<T, true><<<grid, 256, 0, st>>>(L, src, m, occ, A, err);
+    else k_gather<T, false><<<grid, 256, 0, st>>>(L, src, m, occ, A, err);
+}
+
+#if !defined(LRU_INST_DTYPE) || defined(LRU_INST_PRIMARY)
+__global__ void k_commit_moves(int W, int n, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
+                               const int* pst) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    if (mask && !mask[w]) return;
+    if (pst && pst[w] != 4) return;   // 4: consumed by an accept
+    const int i = slot[w];
+    if (i >= 0 && i < n) occ[(long long)w * n + i] = newrow[w];
+}
+#endif
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_propose(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& U,
+                    const DevOperand& V, const T* C, T* ratio_out, int* st_out, cudaStream_t st) {
+    const size_t dyn = delayed ? (size_t)L.Kc * MAXKK * sizeof(T) : 0;
+    const unsigned all = (L.kk >= 32) ? 0xffffffffu : ((1u << L.kk) - 1u);
+    if (delayed && (U.mask & all) != all)
+        k_qtu_dense<T><<<dim3(L.W, L.kk), PT, 0, st>>>(L, S, U);
+    if (!pf && !delayed) k_propose<T, false, false><<<L.W, PT, dyn, st>>>(L, S, U, V, C, ratio_out, st_out);
+    if (!pf && delayed) {
+        cudaFuncSetAttribute(k_propose<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        k_propose<T, false, true><<<L.W, PT, dyn, st>>>(L, S, U, V, C, ratio_out, st_out);
+    }
+    if (pf && !delayed) k_propose<T, true, false><<<L.W, PT, dyn, st>>>(L, S, U, V, C, ratio_out, st_out);
+    if (pf && delayed) {
+        cudaFuncSetAttribute(k_propose<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        k_propose<T, true, true><<<L.W, PT, dyn, st>>>(L, S, U, V, C, ratio_out, st_out);
+    }
+}
+
+template <typename T, bool DELAYED>
+static void accept_npl(int npl, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
+                       const uint8_t* mask, const int* items, int nitems, size_t dyn, cudaStream_t st) {
+    const int4* it = reinterpret_cast<const int4*>(items);
+#define LRU_ACC(N)                                                                                      \
+    case N:                                                                                             \
+        cudaFuncSetAttribute(k_accept<T, DELAYED, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn); \
+        k_accept<T, DELAYED, N><<<nitems, PT, dyn, st>>>(L, S, V, mask, it);                             \
+        break;
+    switch (npl) {
+        LRU_ACC(1) LRU_ACC(2) LRU_ACC(4) LRU_ACC(8) LRU_ACC(16) LRU_ACC(32) LRU_ACC(64)
+        default: break;
+    }
+#undef LRU_ACC
+}
+
+template <typename T>
+void launch_accept(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
+                   const uint8_t* mask, const int* items, int nitems, cudaStream_t st) {
+    (void)pf;
+    const int nmax = L.n_max;
+    int npl = 1;
+    while (32 * npl < nmax) npl *= 2;
+    size_t dyn = (size_t)2 * L.kk * nmax * sizeof(T);
+    if (dyn > 160 * 1024) dyn = 0;   // items carry use_smem = 0 in that case (set by the API)
+    if (nitems > 0) {
+        if (delayed) accept_npl<T, true>(npl, L, S, V, mask, items, nitems, dyn, st);
+        else accept_npl<T, false>(npl, L, S, V, mask, items, nitems, dyn, st);
+    }
+    k_commit<T><<<(L.W + 255) / 256, 256, 0, st>>>(L, S, mask, delayed);
+}
+
+template <typename T>
+void launch_flush_native(bool pf, const DevLayout& L, const DevState<T>& S, const uint8_t* force_mask,
+                         int nmax, cudaStream_t st) {
+    const int nt = (nmax + 31) / 32;
+    dim3 grid(nt, nt, L.W);
+    if (pf) k_flush_native<T, true><<<grid, 256, 0, st>>>(L, S, force_mask);
+    else k_flush_native<T, false><<<grid, 256, 0, st>>>(L, S, force_mask);
+}
+
+template <typename T>
+void launch_flush_finish(const DevLayout& L, const DevState<T>& S, const uint8_t* force_mask, cudaStream_t st) {
+    k_flush_finish<T><<<(L.W + 255) / 256, 256, 0, st>>>(L, S, force_mask);
+}
+
+template <typename T>
+void launch_set_delay_zero(const DevLayout& L, const DevState<T>& S, cudaStream_t st) {
+    k_set_delay_zero<T><<<(L.W + 255) / 256, 256, 0, st>>>(L, S);
+}
+
+template <typename T>
+void launch_get_inverse(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, T* out,
+                        cudaStream_t st) {
+    const int nt = (L.n_max + 31) / 32;
+    dim3 grid(nt, nt, L.W);
+    if (!pf && !delayed) k_get_inverse<T, false, false><<<grid, 256, 0, st>>>(L, S, out);
+    if (!pf && delayed) k_get_inverse<T, false, true><<<grid, 256, 0, st>>>(L, S, out);
+    if (pf && !delayed) k_get_inverse<T, true, false><<<grid, 256, 0, st>>>(L, S, out);
+    if (pf && delayed) k_get_inverse<T, true, true><<<grid, 256, 0, st>>>(L, S, out);
+}
+
+template <typename T>
+void launch_form_row_moves(const DevLayout& L, const T* Phi, int m, const int* occ, const int* slot,
+                           const int* newrow, T* Vout, int* idx, cudaStream_t st) {
+    k_form_row_moves<T><<<L.W, 256, 0, st>>>(L, Phi, m, occ, slot, newrow, Vout, idx);
+}
+
+template <typename T>
+void launch_form_pf_moves(const DevLayout& L, const T* F, int m, const int* pos, const int* slot,
+                          const int* newsite, T* Bout, int* idx, cudaStream_t st) {
+    k_form_pf_moves<T><<<L.W, 256, 0, st>>>(L, F, m, pos, slot, newsite, Bout, idx);
+}
+
+#if !defined(LRU_INST_DTYPE) || defined(LRU_INST_PRIMARY)
+void launch_commit_moves(int W, int n, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
+                         const int* pst, cudaStream_t st) {
+    k_commit_moves<<<(W + 255) / 256, 256, 0, st>>>(W, n, occ, slot, newrow, mask, pst);
+}
+#endif
+
+#define LRU_INST(T)                                                                                          \
+    template void launch_propose<T>(bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&,    \
+                                    const DevOperand&, const T*, T*, int*, cudaStream_t);                   \
+    template void launch_accept<T>(bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&,     \
+                                   const uint8_t*, const int*, int, cudaStream_t);                          \
+    template void launch_flush_native<T>(bool, const DevLayout&, const DevState<T>&, const uint8_t*, int,   \
+                                         cudaStream_t);                                                     \
+    template void launch_flush_finish<T>(const DevLayout&, const DevState<T>&, const uint8_t*, cudaStream_t); \
+    template void launch_set_delay_zero<T>(const DevLayout&, const DevState<T>&, cudaStream_t);             \
+    template void launch_get_inverse<T>(bool, bool, const DevLayout&, const DevState<T>&, T*, cudaStream_t); \
+    template void launch_form_row_moves<T>(const DevLayout&, const T*, int, const int*, const int*,         \
+                                           const int*, T*, int*, cudaStream_t);                             \
+    template void launch_form_pf_moves<T>(const DevLayout&, const T*, int, const int*, const int*,          \
+                                          const int*, T*, int*, cudaStream_t);                              \
+    template void launch_gather<T>(bool, const DevLayout&, const T*, int, const int*, T*, int*, cudaStream_t);
+
+// The build compiles this file once per dtype (LRU_INST_DTYPE) in parallel.
+#if defined(LRU_INST_DTYPE)
+LRU_INST(LRU_INST_DTYPE)
+#else
+LRU_INST(double)
+LRU_INST(float)
+LRU_INST(c128)
+LRU_INST(c64)
+#endif
+
+}  // namespace lru

@@ -1,0 +1,692 @@
+// C-ABI of the library (include/lrugb.h): argument validation, state
+// allocation, and the launch sequence of each call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lrugb.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace lru;
+
+namespace {
+
+constexpr int MAXKK = 16;
+constexpr int MAXN = 2048;
+constexpr int MAXKC = 64;
+
+size_t dtype_size(int d) {
+    switch (d) {
+        case LRU_F64: return 8;
+        case LRU_C128: return 16;
+        case LRU_F32: return 4;
+        case LRU_C64: return 8;
+        default: return 0;
+    }
+}
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct lru_ctx {
+    lru_config cfg;
+    int dtype = 0;
+    bool pf = false, delayed = false;
+    int W = 0, kk = 0, K = 0, Kc = 0, flush = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n_uni = 0, n_max = 0;
+    std::vector<int> n_h, kv_h;
+    std::vector<long long> moff_h, voff_h;
+    long long sum_n = 0, sum_n2 = 0;
+    // device memory
+    unsigned char* base = nullptr;
+    size_t bytes = 0, persist_bytes = 0;
+    int* d_n = nullptr;
+    long long* d_moff = nullptr;
+    long long* d_voff = nullptr;
+    int* d_kv = nullptr;
+    int* d_items = nullptr;
+    int nitems = 0;
+    bool items_smem = true;
+    void *G = nullptr, *P = nullptr, *Q = nullptr;
+    float *P32h = nullptr, *P32l = nullptr, *Q32h = nullptr, *Q32l = nullptr;
+    int* tau = nullptr;
+    double* logabs = nullptr;
+    void* sgn = nullptr;
+    void *X = nullptr, *Rinv = nullptr, *ratio = nullptr, *VP = nullptr, *QtU = nullptr;
+    int* pst = nullptr;
+    int* err = nullptr;
+    // refresh workspace (allocated on first use)
+    void* ws = nullptr;
+    int nws = 0;
+    // profiling: event pairs per kernel class, and a launch counter
+    bool prof_on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[4];
+    size_t prof_used[4] = {0, 0, 0, 0};
+    long long launches = 0;
+    // last proposal
+    bool has_prop = false;
+    DevOperand lastV{};
+    int n_sm = 148;
+
+    DevLayout layout() const {
+        DevLayout L;
+        L.W = W;
+        L.n_uni = n_uni;
+        L.n_max = n_max;
+        L.n = d_n;
+        L.moff = d_moff;
+        L.voff = d_voff;
+        L.kk = kk;
+        L.kvec = d_kv;
+        L.Kc = Kc;
+        L.K = K;
+        return L;
+    }
+    template <typename T>
+    DevState<T> state() const {
+        DevState<T> S;
+        S.G = (T*)G;
+        S.P = (T*)P;
+        S.Q = (T*)Q;
+        S.P32h = P32h;
+        S.P32l = P32l;
+        S.Q32h = Q32h;
+        S.Q32l = Q32l;
+        S.tau = tau;
+        S.logabs = logabs;
+        S.sgn = (T*)sgn;
+        S.X = (T*)X;
+        S.Rinv = (T*)Rinv;
+        S.ratio = (T*)ratio;
+        S.pst = pst;
+        S.VP = (T*)VP;
+        S.QtU = (T*)QtU;
+        S.err = err;
+        return S;
+    }
+};
+
+#define LRU_DISPATCH(ctx, ...)                      \
+    switch ((ctx)->dtype) {                         \
+        case LRU_F64: { using T = double; __VA_ARGS__; } break;   \
+        case LRU_C128: { using T = lru::c128; __VA_ARGS__; } break; \
+        case LRU_F32: { using T = float; __VA_ARGS__; } break;    \
+        case LRU_C64: { using T = lru::c64; __VA_ARGS__; } break; \
+        default: return LRU_ERR_ARG;                \
+    }
+
+static lru_status cuda_check() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LRU_OK : LRU_ERR_CUDA;
+}
+
+#define CK(call)                                                     \
+    do {                                                             \
+        if ((call) != cudaSuccess) { cudaGetLastError(); return LRU_ERR_CUDA; } \
+    } while (0)
+
+static void prof_begin(lru_ctx* h, int cls) {
+    if (!h->prof_on) return;
+    auto& v = h->prof_ev[cls];
+    if (h->prof_used[cls] == v.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) { cudaGetLastError(); return; }
+        v.emplace_back(a, b);
+    }
+    cudaEventRecord(v[h->prof_used[cls]].first, h->stream);
+}
+
+static void prof_end(lru_ctx* h, int cls) {
+    if (!h->prof_on) return;
+    auto& v = h->prof_ev[cls];
+    if (h->prof_used[cls] < v.size()) cudaEventRecord(v[h->prof_used[cls]++].second, h->stream);
+}
+
+static lru_status ensure_ws(lru_ctx* h) {
+    if (h->ws) return LRU_OK;
+    int nws = std::min(h->W, 2 * h->n_sm);
+    size_t b = (size_t)nws * h->n_max * h->n_max * dtype_size(h->dtype);
+    if (cudaMalloc(&h->ws, b) != cudaSuccess) {
+        cudaGetLastError();
+        h->ws = nullptr;
+        return LRU_ERR_NOMEM;
+    }
+    h->nws = nws;
+    return LRU_OK;
+}
+
+extern "C" {
+
+const char* lru_status_string(lru_status s) {
+    switch (s) {
+        case LRU_OK: return "ok";
+        case LRU_ERR_ARG: return "invalid argument";
+        case LRU_ERR_CUDA: return "CUDA runtime error";
+        case LRU_ERR_NOMEM: return "device allocation failed";
+        case LRU_ERR_STATE: return "call out of order";
+        case LRU_ERR_SINGULAR: return "singular matrix";
+        case LRU_ERR_NOT_SKEW: return "matrix is not skew-symmetric";
+        case LRU_ERR_TIMEOUT: return "bounded device wait gave up";
+        case LRU_ERR_UNSUPPORTED: return "combination not supported";
+    }
+    return "unknown status";
+}
+
+const char* lru_version(void) { return "lrugb 0.1.0 sm_103a"; }
+
+lru_status lru_create(const lru_config* cfg, lru_handle* out) {
+    if (!cfg || !out) return LRU_ERR_ARG;
+    *out = nullptr;
+    if (cfg->kind != LRU_DET && cfg->kind != LRU_PF) return LRU_ERR_ARG;
+    if (dtype_size(cfg->dtype) == 0) return LRU_ERR_ARG;
+    if (cfg->walkers < 1 || cfg->walkers > (1 << 24)) return LRU_ERR_ARG;
+    if (cfg->k < 1) return LRU_ERR_ARG;
+    const int kk = cfg->kind == LRU_PF ? 2 * cfg->k : cfg->k;
+    if (kk > MAXKK) return LRU_ERR_ARG;
+    if (cfg->delay < 0) return LRU_ERR_ARG;
+    if (cfg->flush < LRU_FLUSH_NATIVE || cfg->flush > LRU_FLUSH_BF16X3) return LRU_ERR_ARG;
+    const bool delayed = cfg->delay >= 2;
+    if (delayed && cfg->delay * kk > MAXKC) return LRU_ERR_ARG;
+    if (cfg->flush != LRU_FLUSH_NATIVE && !(delayed && cfg->dtype == LRU_F64)) return LRU_ERR_UNSUPPORTED;
+
+    lru_ctx* h = new (std::nothrow) lru_ctx();
+    if (!h) return LRU_ERR_NOMEM;
+    h->cfg = *cfg;
+    h->cfg.n_per_walker = nullptr;
+    h->cfg.k_per_walker = nullptr;
+    h->dtype = cfg->dtype;
+    h->pf = cfg->kind == LRU_PF;
+    h->delayed = delayed;
+    h->W = (int)cfg->walkers;
+    h->kk = kk;
+    h->K = delayed ? cfg->delay : 0;
+    h->Kc = delayed ? cfg->delay * kk : 0;
+    h->flush = cfg->flush;
+    h->device = cfg->device;
+
+    // geometry
+    h->n_h.resize(h->W);
+    h->kv_h.resize(h->W);
+    for (int w = 0; w < h->W; ++w) {
+        int n = cfg->n_per_walker ? cfg->n_per_walker[w] : cfg->n;
+        int kw = cfg->k_per_walker ? cfg->k_per_walker[w] : cfg->k;
+        if (n < 1 || n > MAXN || kw < 1 || kw > cfg->k || (h->pf && (n & 1))) {
+            delete h;
+            return LRU_ERR_ARG;
+        }
+        h->n_h[w] = n;
+        h->kv_h[w] = h->pf ? 2 * kw : kw;
+    }
+    bool uniform = true;
+    for (int w = 1; w < h->W; ++w) uniform = uniform && h->n_h[w] == h->n_h[0];
+    h->n_uni = uniform ? h->n_h[0] : 0;
+    h->n_max = *std::max_element(h->n_h.begin(), h->n_h.end());
+    h->moff_h.resize(h->W);
+    h->voff_h.resize(h->W);
+    for (int w = 0; w < h->W; ++w) {
+        h->moff_h[w] = h->sum_n2;
+        h->voff_h[w] = h->sum_n;
+        h->sum_n2 += (long long)h->n_h[w] * h->n_h[w];
+        h->sum_n += h->n_h[w];
+    }
+    bool kuni = true;
+    for (int w = 0; w < h->W; ++w) kuni = kuni && h->kv_h[w] == kk;
+    if (!uniform && h->pf) { /* ragged Pfaffian handles are allowed */ }
+
+    if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); delete h; return LRU_ERR_CUDA; }
+    {
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess && nsm > 0)
+            h->n_sm = nsm;
+        cudaGetLastError();
+    }
+
+    // accept work items: (walker, first chunk, end chunk, use_smem)
+    std::vector<int> items;
+    const size_t sz = dtype_size(h->dtype);
+    h->items_smem = (size_t)2 * kk * h->n_max * sz <= 160 * 1024;
+    for (int w = 0; w < h->W; ++w) {
+        const int n = h->n_h[w];
+        const int ch = std::max(8, std::min(64, n / 4));
+        for (int l0 = 0; l0 < n; l0 += ch) {
+            items.push_back(w);
+            items.push_back(l0);
+            items.push_back(std::min(n, l0 + ch));
+            items.push_back(h->items_smem ? 1 : 0);
+        }
+    }
+    h->nitems = (int)items.size() / 4;
+
+    // one allocation: persistent state first, then scratch and metadata
+    const bool tc = delayed && cfg->flush != LRU_FLUSH_NATIVE;
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = align_up(off + b); return o; };
+    const size_t oG = take((size_t)h->sum_n2 * sz);
+    const size_t oP = delayed ? take((size_t)h->sum_n * h->Kc * sz) : 0;
+    const size_t oQ = delayed ? take((size_t)h->sum_n * h->Kc * sz) : 0;
+    const size_t o32 = tc ? take((size_t)4 * h->sum_n * h->Kc * sizeof(float)) : 0;
+    const size_t oTau = take((size_t)h->W * sizeof(int));
+    const size_t oLog = take((size_t)h->W * sizeof(double));
+    const size_t oSgn = take((size_t)h->W * sz);
+    h->persist_bytes = off;
+    const size_t oX = take((size_t)h->sum_n * kk * sz);
+    const size_t oRinv = take((size_t)h->W * MAXKK * MAXKK * sz);
+    const size_t oRatio = take((size_t)h->W * sz);
+    const size_t oPst = take((size_t)h->W * sizeof(int));
+    const size_t oVP = delayed ? take((size_t)h->W * MAXKK * h->Kc * sz) : 0;
+    const size_t oQtU = delayed ? take((size_t)h->W * h->Kc * MAXKK * sz) : 0;
+    const size_t oErr = take(sizeof(int));
+    const size_t oN = take((size_t)h->W * sizeof(int));
+    const size_t oMoff = take((size_t)h->W * sizeof(long long));
+    const size_t oVoff = take((size_t)h->W * sizeof(long long));
+    const size_t oKv = take((size_t)h->W * sizeof(int));
+    const size_t oItems = take(items.size() * sizeof(int));
+    h->bytes = off;
+    if (cudaMalloc(&h->base, h->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return LRU_ERR_NOMEM;
+    }
+    unsigned char* b = h->base;
+    h->G = b + oG;
+    if (delayed) { h->P = b + oP; h->Q = b + oQ; }
+    if (tc) {
+        const size_t e = (size_t)h->sum_n * h->Kc;
+        h->P32h = (float*)(b + o32);
+        h->P32l = h->P32h + e;
+        h->Q32h = h->P32l + e;
+        h->Q32l = h->Q32h + e;
+    }
+    h->tau = (int*)(b + oTau);
+    h->logabs = (double*)(b + oLog);
+    h->sgn = b + oSgn;
+    h->X = b + oX;
+    h->Rinv = b + oRinv;
+    h->ratio = b + oRatio;
+    h->pst = (int*)(b + oPst);
+    if (delayed) { h->VP = b + oVP; h->QtU = b + oQtU; }
+    h->err = (int*)(b + oErr);
+    h->d_n = (int*)(b + oN);
+    h->d_moff = (long long*)(b + oMoff);
+    h->d_voff = (long long*)(b + oVoff);
+    h->d_kv = kuni ? nullptr : (int*)(b + oKv);
+    h->d_items = (int*)(b + oItems);
+    lru_status s = LRU_OK;
+    if (cudaMemset(h->base, 0, h->bytes) != cudaSuccess ||
+        cudaMemcpy(h->d_n, h->n_h.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_moff, h->moff_h.data(), h->W * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_voff, h->voff_h.data(), h->W * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b + oKv, h->kv_h.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        s = LRU_ERR_CUDA;
+    if (s != LRU_OK) {
+        cudaGetLastError();
+        cudaFree(h->base);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return LRU_OK;
+}
+
+lru_status lru_destroy(lru_handle h) {
+    if (!h) return LRU_ERR_ARG;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(h->base);
+    if (h->ws) cudaFree(h->ws);
+    for (auto& v : h->prof_ev)
+        for (auto& e : v) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    cudaGetLastError();
+    delete h;
+    return LRU_OK;
+}
+
+lru_status lru_set_stream(lru_handle h, void* stream) {
+    if (!h) return LRU_ERR_ARG;
+    h->stream = (cudaStream_t)stream;
+    return LRU_OK;
+}
+
+lru_status lru_device_bytes(lru_handle h, size_t* bytes) {
+    if (!h || !bytes) return LRU_ERR_ARG;
+    *bytes = h->bytes + (h->ws ? (size_t)h->nws * h->n_max * h->n_max * dtype_size(h->dtype) : 0);
+    return LRU_OK;
+}
+
+static lru_status do_init(lru_handle h, const void* A, const uint8_t* mask, double* drift, double* logabs_out,
+                          void* sign_out, bool with_ws) {
+    if (!A) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    if (with_ws || h->pf) {
+        lru_status s = ensure_ws(h);
+        if (s != LRU_OK) return s;
+    }
+    DevLayout L = h->layout();
+    prof_begin(h, LRU_PROF_REFRESH);
+    h->launches += h->pf ? 2 : 1;
+    LRU_DISPATCH(h, {
+        DevState<T> S = h->state<T>();
+        launch_refresh<T>(h->pf, h->delayed, L, S, (const T*)A, mask, with_ws ? (T*)h->ws : nullptr, h->nws,
+                          drift, !h->pf, h->stream);
+        if (h->pf) launch_slogpf<T>(L, (const T*)A, mask, (T*)h->ws, h->nws, S.logabs, S.sgn, h->stream);
+    });
+    prof_end(h, LRU_PROF_REFRESH);
+    lru_status s = cuda_check();
+    if (s != LRU_OK) return s;
+    const size_t sz = dtype_size(h->dtype);
+    if (logabs_out) CK(cudaMemcpyAsync(logabs_out, h->logabs, h->W * sizeof(double), cudaMemcpyDefault, h->stream));
+    if (sign_out) CK(cudaMemcpyAsync(sign_out, h->sgn, h->W * sz, cudaMemcpyDefault, h->stream));
+    h->has_prop = false;
+    return LRU_OK;
+}
+
+lru_status lru_init_det(lru_handle h, const void* A, double* logabs, void* sign) {
+    if (!h) return LRU_ERR_ARG;
+    if (h->pf) return LRU_ERR_STATE;
+    return do_init(h, A, nullptr, nullptr, logabs, sign, false);
+}
+
+lru_status lru_init_pf(lru_handle h, const void* A, double* logabs, void* sign) {
+    if (!h) return LRU_ERR_ARG;
+    if (!h->pf) return LRU_ERR_STATE;
+    return do_init(h, A, nullptr, nullptr, logabs, sign, false);
+}
+
+lru_status lru_refresh_from_scratch(lru_handle h, const void* A, const uint8_t* mask, double* drift) {
+    if (!h) return LRU_ERR_ARG;
+    return do_init(h, A, mask, drift, nullptr, nullptr, true);
+}
+
+static bool operand_ok(const lru_operand* o, int kk) {
+    if (!o) return false;
+    const unsigned all = (kk >= 32) ? 0xffffffffu : ((1u << kk) - 1u);
+    const unsigned m = o->onehot_mask & all;
+    if (m != 0 && !o->idx) return false;
+    if (m != all && !o->dense) return false;
+    return true;
+}
+
+lru_status lru_propose_det(lru_handle h, const lru_operand* U, const lru_operand* V, void* ratio, int32_t* st) {
+    if (!h || !ratio) return LRU_ERR_ARG;
+    if (h->pf) return LRU_ERR_STATE;
+    if (!operand_ok(U, h->kk) || !operand_ok(V, h->kk)) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    DevOperand dU{U->dense, U->idx, U->onehot_mask, h->kk};
+    DevOperand dV{V->dense, V->idx, V->onehot_mask, h->kk};
+    DevLayout L = h->layout();
+    const unsigned all = (1u << h->kk) - 1u;
+    h->launches += 1 + ((h->delayed && (dU.mask & all) != all) ? 1 : 0);
+    prof_begin(h, LRU_PROF_PROPOSE);
+    LRU_DISPATCH(h, {
+        launch_propose<T>(false, h->delayed, L, h->state<T>(), dU, dV, nullptr, (T*)ratio, st, h->stream);
+    });
+    prof_end(h, LRU_PROF_PROPOSE);
+    lru_status s = cuda_check();
+    if (s != LRU_OK) return s;
+    h->lastV = dV;
+    h->has_prop = true;
+    return LRU_OK;
+}
+
+lru_status lru_propose_pf(lru_handle h, const lru_operand* B, const void* C, void* ratio, int32_t* st) {
+    if (!h || !ratio) return LRU_ERR_ARG;
+    if (!h->pf) return LRU_ERR_STATE;
+    if (!operand_ok(B, h->kk)) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    DevOperand dB{B->dense, B->idx, B->onehot_mask, h->kk};
+    DevLayout L = h->layout();
+    const unsigned all = (1u << h->kk) - 1u;
+    h->launches += 1 + ((h->delayed && (dB.mask & all) != all) ? 1 : 0);
+    prof_begin(h, LRU_PROF_PROPOSE);
+    LRU_DISPATCH(h, {
+        launch_propose<T>(true, h->delayed, L, h->state<T>(), dB, dB, (const T*)C, (T*)ratio, st, h->stream);
+    });
+    prof_end(h, LRU_PROF_PROPOSE);
+    lru_status s = cuda_check();
+    if (s != LRU_OK) return s;
+    h->lastV = dB;
+    h->has_prop = true;
+    return LRU_OK;
+}
+
+static lru_status do_flush(lru_handle h, const uint8_t* force) {
+    DevLayout L = h->layout();
+    prof_begin(h, LRU_PROF_FLUSH);
+    h->launches += 2;
+    if (h->flush != LRU_FLUSH_NATIVE) {
+        if (!launch_flush_tc(h->flush, h->pf, L, (double*)h->G, h->P32h, h->P32l, h->Q32h, h->Q32l, h->tau,
+                             force, h->err, h->stream))
+            return LRU_ERR_UNSUPPORTED;
+    } else {
+        LRU_DISPATCH(h, { launch_flush_native<T>(h->pf, L, h->state<T>(), force, h->n_max, h->stream); });
+    }
+    prof_end(h, LRU_PROF_FLUSH);
+    LRU_DISPATCH(h, { launch_flush_finish<T>(L, h->state<T>(), force, h->stream); });
+    return cuda_check();
+}
+
+lru_status lru_accept(lru_handle h, const uint8_t* mask) {
+    if (!h) return LRU_ERR_ARG;
+    if (!h->has_prop) return LRU_ERR_STATE;
+    CK(cudaSetDevice(h->device));
+    DevLayout L = h->layout();
+    // the delayed Pfaffian wrote both slots at propose time: no pass over A_0^{-1}
+    const int nitems = (h->pf && h->delayed) ? 0 : h->nitems;
+    h->launches += (nitems > 0 ? 1 : 0) + 1;
+    prof_begin(h, LRU_PROF_ACCEPT);
+    LRU_DISPATCH(h, {
+        launch_accept<T>(h->pf, h->delayed, L, h->state<T>(), h->lastV, mask, h->d_items, nitems, h->stream);
+    });
+    prof_end(h, LRU_PROF_ACCEPT);
+    lru_status s = cuda_check();
+    if (s != LRU_OK) return s;
+    if (h->delayed) return do_flush(h, nullptr);
+    return LRU_OK;
+}
+
+lru_status lru_flush_delayed(lru_handle h, const uint8_t* mask) {
+    if (!h) return LRU_ERR_ARG;
+    if (!h->delayed) return LRU_OK;
+    CK(cudaSetDevice(h->device));
+    if (!mask) {
+        // all walkers: a device mask of ones
+        uint8_t* ones = nullptr;
+        CK(cudaMallocAsync((void**)&ones, h->W, h->stream));
+        CK(cudaMemsetAsync(ones, 1, h->W, h->stream));
+        lru_status s = do_flush(h, ones);
+        cudaFreeAsync(ones, h->stream);
+        return s;
+    }
+    return do_flush(h, mask);
+}
+
+lru_status lru_get_inverse(lru_handle h, void* out) {
+    if (!h || !out) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    DevLayout L = h->layout();
+    h->launches += 1;
+    LRU_DISPATCH(h, { launch_get_inverse<T>(h->pf, h->delayed, L, h->state<T>(), (T*)out, h->stream); });
+    return cuda_check();
+}
+
+lru_status lru_get_logvalue(lru_handle h, double* logabs, void* sign) {
+    if (!h) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    if (logabs) CK(cudaMemcpyAsync(logabs, h->logabs, h->W * sizeof(double), cudaMemcpyDefault, h->stream));
+    if (sign) CK(cudaMemcpyAsync(sign, h->sgn, h->W * dtype_size(h->dtype), cudaMemcpyDefault, h->stream));
+    return LRU_OK;
+}
+
+lru_status lru_get_delay(lru_handle h, int32_t* tau) {
+    if (!h || !tau) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpyAsync(tau, h->tau, h->W * sizeof(int), cudaMemcpyDefault, h->stream));
+    return LRU_OK;
+}
+
+lru_status lru_state_bytes(lru_handle h, size_t* bytes) {
+    if (!h || !bytes) return LRU_ERR_ARG;
+    *bytes = h->persist_bytes;
+    return LRU_OK;
+}
+
+lru_status lru_save_state(lru_handle h, void* buf) {
+    if (!h || !buf) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpyAsync(buf, h->base, h->persist_bytes, cudaMemcpyDefault, h->stream));
+    return LRU_OK;
+}
+
+lru_status lru_load_state(lru_handle h, const void* buf) {
+    if (!h || !buf) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpyAsync(h->base, buf, h->persist_bytes, cudaMemcpyDefault, h->stream));
+    h->has_prop = false;
+    return LRU_OK;
+}
+
+lru_status lru_check_device_error(lru_handle h) {
+    if (!h) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    int e = 0;
+    CK(cudaMemcpy(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) CK(cudaMemset(h->err, 0, sizeof(int)));
+    if (e == DEV_ERR_TIMEOUT) return LRU_ERR_TIMEOUT;
+    if (e) return LRU_ERR_CUDA;
+    return LRU_OK;
+}
+
+lru_status lru_form_row_moves(lru_handle h, const void* Phi, int32_t m, const int32_t* occ, const int32_t* slot,
+                              const int32_t* new_row, void* V_out, int32_t* idx_out) {
+    if (!h || !Phi || !occ || !slot || !new_row || !V_out || !idx_out || m < 1) return LRU_ERR_ARG;
+    if (h->pf || h->n_uni <= 0 || h->kk != 1) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    DevLayout L = h->layout();
+    h->launches += 1;
+    LRU_DISPATCH(h, {
+        launch_form_row_moves<T>(L, (const T*)Phi, m, occ, slot, new_row, (T*)V_out, idx_out, h->stream);
+    });
+    return cuda_check();
+}
+
+lru_status lru_form_pf_moves(lru_handle h, const void* F, int32_t m, const int32_t* pos, const int32_t* slot,
+                             const int32_t* new_site, void* B_out, int32_t* idx_out) {
+    if (!h || !F || !pos || !slot || !new_site || !B_out || !idx_out || m < 1) return LRU_ERR_ARG;
+    if (!h->pf || h->n_uni <= 0 || h->kk != 2) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    DevLayout L = h->layout();
+    h->launches += 1;
+    LRU_DISPATCH(h, {
+        launch_form_pf_moves<T>(L, (const T*)F, m, pos, slot, new_site, (T*)B_out, idx_out, h->stream);
+    });
+    return cuda_check();
+}
+
+lru_status lru_commit_moves(lru_handle h, int32_t* occ, const int32_t* slot, const int32_t* new_row,
+                            const uint8_t* mask) {
+    if (!h || !occ || !slot || !new_row) return LRU_ERR_ARG;
+    if (h->n_uni <= 0) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    h->launches += 1;
+    launch_commit_moves(h->W, h->n_uni, occ, slot, new_row, mask, h->pst, h->stream);
+    return cuda_check();
+}
+
+lru_status lru_gather_rows(lru_handle h, const void* Phi, int32_t m, const int32_t* occ, void* A_out) {
+    if (!h || !Phi || !occ || !A_out || m < 1) return LRU_ERR_ARG;
+    if (h->n_uni <= 0) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    DevLayout L = h->layout();
+    h->launches += 1;
+    LRU_DISPATCH(h, { launch_gather<T>(false, L, (const T*)Phi, m, occ, (T*)A_out, h->err, h->stream); });
+    return cuda_check();
+}
+
+lru_status lru_gather_pairs(lru_handle h, const void* F, int32_t m, const int32_t* pos, void* A_out) {
+    if (!h || !F || !pos || !A_out || m < 1) return LRU_ERR_ARG;
+    if (h->n_uni <= 0) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    DevLayout L = h->layout();
+    h->launches += 1;
+    LRU_DISPATCH(h, { launch_gather<T>(true, L, (const T*)F, m, pos, (T*)A_out, h->err, h->stream); });
+    return cuda_check();
+}
+
+lru_status lru_profile_enable(lru_handle h, int32_t on) {
+    if (!h) return LRU_ERR_ARG;
+    h->prof_on = on != 0;
+    return LRU_OK;
+}
+
+lru_status lru_profile_read(lru_handle h, int32_t cls, double* total_ms, int64_t* launches) {
+    if (!h || cls < 0 || cls >= LRU_PROF_CLASSES) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    double t = 0.0;
+    const size_t used = h->prof_used[cls];
+    for (size_t i = 0; i < used; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->prof_ev[cls][i].first, h->prof_ev[cls][i].second));
+        t += ms;
+    }
+    h->prof_used[cls] = 0;
+    if (total_ms) *total_ms = t;
+    if (launches) *launches = (int64_t)used;
+    return LRU_OK;
+}
+
+lru_status lru_launch_count(lru_handle h, int64_t* count) {
+    if (!h || !count) return LRU_ERR_ARG;
+    *count = h->launches;
+    return LRU_OK;
+}
+
+static lru_status batched_dense(bool pf, int32_t dtype, int64_t W, int32_t n, const void* A, double* logabs,
+                                void* sign, void* stream) {
+    if (W < 1 || n < 1 || n > MAXN || !A || !logabs || !sign || dtype_size(dtype) == 0) return LRU_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 148;
+    CK(cudaGetDevice(&dev));
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { cudaGetLastError(); nsm = 148; }
+    const int nws = (int)std::min<int64_t>(W, 2 * nsm);
+    void* ws = nullptr;
+    CK(cudaMallocAsync(&ws, (size_t)nws * n * n * dtype_size(dtype), st));
+    lru_ctx tmp;
+    tmp.dtype = dtype;
+    DevLayout L{};
+    L.W = (int)W;
+    L.n_uni = n;
+    L.n_max = n;
+    lru_ctx* h = &tmp;
+    LRU_DISPATCH(h, {
+        if (pf) launch_slogpf<T>(L, (const T*)A, nullptr, (T*)ws, nws, logabs, (T*)sign, st);
+        else launch_slogdet<T>((int)W, n, (const T*)A, (T*)ws, nws, logabs, (T*)sign, st);
+    });
+    lru_status s = cuda_check();
+    cudaFreeAsync(ws, st);
+    return s;
+}
+
+lru_status lru_slogdet_batched(int32_t dtype, int64_t W, int32_t n, const void* A, double* logabs, void* sign,
+                               void* stream) {
+    return batched_dense(false, dtype, W, n, A, logabs, sign, stream);
+}
+
+lru_status lru_slogpf_batched(int32_t dtype, int64_t W, int32_t n, const void* A, double* logabs, void* sign,
+                              void* stream) {
+    if (n & 1) return LRU_ERR_ARG;
+    return batched_dense(true, dtype, W, n, A, logabs, sign, stream);
+}
+
+}  // extern "C"

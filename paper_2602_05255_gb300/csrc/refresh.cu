@@ -1,0 +1,448 @@
+// From-scratch inverse, log|det| and Pfaffian of the walker matrices: the
+// initial carrier (Sec. 2.3 init_det_carrier, Sec. 3.3 init_pf_carrier) and
+// the periodic refresh that bounds the drift of the update chain (Sec. 2.1
+// advises double precision against accumulated error).  Always run in the
+// handle dtype (FP64 / complex128 for the double types).
+#include "common.cuh"
+#include "internal.h"
+
+namespace lru {
+
+constexpr int RT = 256;   // threads per matrix
+constexpr int GB = 16;    // Gauss-Jordan panel width
+
+__device__ void block_argmax(double v, int i, double* sv, int* si, double& bv, int& bi) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ov > v || (ov == v && oi >= 0 && (i < 0 || oi < i))) { v = ov; i = oi; }
+    }
+    if (lane == 0) { sv[wid] = v; si[wid] = i; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = sv[0];
+        int ib = si[0];
+        for (int q = 1; q < RT / 32; ++q)
+            if (sv[q] > b || (sv[q] == b && si[q] >= 0 && (ib < 0 || si[q] < ib))) { b = sv[q]; ib = si[q]; }
+        sv[0] = b;
+        si[0] = ib;
+    }
+    __syncthreads();
+    bv = sv[0];
+    bi = si[0];
+    __syncthreads();
+}
+
+// Loads M = A^T (A row-major n x n) through 32 x 32 shared-memory tiles.
+template <typename T>
+__device__ void load_transposed(T* M, const T* A, int n, T (*tile)[33]) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int b0 = 0; b0 < n; b0 += 32)
+        for (int b1 = 0; b1 < n; b1 += 32) {
+            for (int q = ty; q < 32; q += RT / 32) {
+                const int r = b0 + q, c = b1 + tx;
+                if (r < n && c < n) tile[q][tx] = A[(long long)r * n + c];
+            }
+            __syncthreads();
+            for (int q = ty; q < 32; q += RT / 32) {
+                const int r = b1 + q, c = b0 + tx;   // M[r][c] = A[c][r]
+                if (r < n && c < n) M[(long long)r * n + c] = tile[tx][q];
+            }
+            __syncthreads();
+        }
+}
+
+// In-place Gauss-Jordan inversion with partial pivoting of the row-major n x n
+// matrix M, blocked in panels of GB columns: each panel is eliminated with the
+// row exchanges restricted to it, then the exchanges and the panel's
+// accumulated transform T = I + sum_c (panel_c - e_c) e_c^T are applied to the
+// other columns as one rank-GB update (a GEMM).  Row exchanges turn into
+// column exchanges of the inverse, undone at the end.  Returns log|det M| and
+// its sign/phase; *singular is set when a pivot is exactly zero.
+template <typename T>
+struct GJSmem {
+    T sS[GB][64];
+    T sPan[64][GB + 1];
+    T tile[32][33];
+};
+
+template <typename T>
+__device__ void gj_invert(T* M, int n, int* perm, double* logabs_out, T* sgn_out, int* singular, GJSmem<T>& sm) {
+    __shared__ double s_v[32];
+    __shared__ int s_i[32];
+    __shared__ T s_rowk[GB];
+    auto& sS = sm.sS;
+    auto& sPan = sm.sPan;
+    __shared__ double s_log;
+    __shared__ T s_sgn;
+    __shared__ int s_sing;
+    const int tid = threadIdx.x;
+    if (tid == 0) { s_log = 0.0; s_sgn = make_real<T>(1.0); s_sing = 0; }
+    __syncthreads();
+
+    for (int k0 = 0; k0 < n; k0 += GB) {
+        const int bw = min(GB, n - k0);
+        // ---- panel ----
+        for (int kc = 0; kc < bw; ++kc) {
+            const int k = k0 + kc;
+            double best = -1.0;
+            int bi = -1;
+            for (int i = k + tid; i < n; i += RT) {
+                double v = (double)s_abs2(M[(long long)i * n + k]);
+                if (v > best) { best = v; bi = i; }
+            }
+            double bv;
+            int p;
+            block_argmax(best, bi, s_v, s_i, bv, p);
+            if (!(bv > 0.0) || p < 0) {
+                if (tid == 0) { perm[k] = k; s_sing = 1; }
+                __syncthreads();
+                continue;
+            }
+            if (tid == 0) perm[k] = p;
+            if (p != k && tid < bw) {
+                T a = M[(long long)k * n + k0 + tid];
+                M[(long long)k * n + k0 + tid] = M[(long long)p * n + k0 + tid];
+                M[(long long)p * n + k0 + tid] = a;
+            }
+            __syncthreads();
+            const T piv = M[(long long)k * n + k];
+            const T ipiv = s_recip(piv);
+            if (tid < bw) {
+                T v = (tid == kc) ? make_real<T>(1.0) : M[(long long)k * n + k0 + tid];
+                v = v * ipiv;
+                s_rowk[tid] = v;
+                M[(long long)k * n + k0 + tid] = v;
+            }
+            if (tid == 0) {
+                s_log += log(s_absd(piv));
+                T sg = s_sgn * s_unit(piv);
+                s_sgn = (p != k) ? s_neg(sg) : sg;
+            }
+            __syncthreads();
+            for (int i = tid; i < n; i += RT) {
+                if (i == k) continue;
+                T* row = M + (long long)i * n + k0;
+                const T f = row[kc];
+                for (int c = 0; c < bw; ++c) {
+                    T v = (c == kc) ? s_zero(T()) : row[c];
+                    row[c] = s_fms(f, s_rowk[c], v);
+                }
+            }
+            __syncthreads();
+        }
+        // ---- the panel's row exchanges on the other columns ----
+        for (int kc = 0; kc < bw; ++kc) {
+            const int k = k0 + kc, p = perm[k];
+            if (p != k)
+                for (int j = tid; j < n; j += RT) {
+                    if (j >= k0 && j < k0 + bw) continue;
+                    T a = M[(long long)k * n + j];
+                    M[(long long)k * n + j] = M[(long long)p * n + j];
+                    M[(long long)p * n + j] = a;
+                }
+            __syncthreads();
+        }
+        // ---- rank-bw update of the other columns: M += (panel - E) S ----
+        const int tx = tid & 15, ty = tid >> 4;   // 16 x 16 threads, 4 x 4 outputs each
+        for (int j0 = 0; j0 < n; j0 += 64) {
+            for (int e = tid; e < GB * 64; e += RT) {
+                const int c = e / 64, jj = e % 64;
+                sS[c][jj] = (c < bw && j0 + jj < n) ? M[(long long)(k0 + c) * n + j0 + jj] : s_zero(T());
+            }
+            __syncthreads();
+            for (int i0 = 0; i0 < n; i0 += 64) {
+                for (int e = tid; e < 64 * GB; e += RT) {
+                    const int ii = e / GB, c = e % GB;
+                    const int i = i0 + ii;
+                    T v = s_zero(T());
+                    if (c < bw && i < n) {
+                        v = M[(long long)i * n + k0 + c];
+                        if (i == k0 + c) v = v - make_real<T>(1.0);
+                    }
+                    sPan[ii][c] = v;
+                }
+                __syncthreads();
+                T acc[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c] = s_zero(T());
+                for (int cc = 0; cc < bw; ++cc) {
+                    T a[4], b[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) a[r] = sPan[ty * 4 + r][cc];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) b[c] = sS[cc][tx * 4 + c];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[r][c] = s_fma(a[r], b[c], acc[r][c]);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int i = i0 + ty * 4 + r;
+                    if (i >= n) continue;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int j = j0 + tx * 4 + c;
+                        if (j >= n || (j >= k0 && j < k0 + bw)) continue;
+                        M[(long long)i * n + j] = M[(long long)i * n + j] + acc[r][c];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    // ---- undo the exchanges as column exchanges, last first ----
+    for (int k = n - 1; k >= 0; --k) {
+        const int p = perm[k];
+        if (p != k)
+            for (int i = tid; i < n; i += RT) {
+                T a = M[(long long)i * n + k];
+                M[(long long)i * n + k] = M[(long long)i * n + p];
+                M[(long long)i * n + p] = a;
+            }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        *logabs_out = s_sing ? -INFINITY : s_log;
+        *sgn_out = s_sing ? s_zero(T()) : s_renorm(s_sgn);
+        *singular = s_sing;
+    }
+    __syncthreads();
+}
+
+// One CTA per (selected) walker.  target: ws slot of the CTA when ws != null
+// (refresh with drift), else the state G itself.
+template <typename T>
+__global__ void __launch_bounds__(RT) k_refresh(DevLayout L, DevState<T> S, const T* A, const uint8_t* mask,
+                                                 T* ws, int nws, double* drift, bool pf, bool delayed,
+                                                 bool write_logdet) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    GJSmem<T>& sm = *reinterpret_cast<GJSmem<T>*>(dsm);
+    __shared__ int perm[2048];
+    __shared__ double s_l;
+    __shared__ T s_s;
+    __shared__ int s_sing;
+    __shared__ double s_red[2][32];
+    for (int w = blockIdx.x; w < L.W; w += gridDim.x) {
+        if (mask && !mask[w]) continue;
+        const int n = L.nw(w);
+        T* G = S.G + L.mo(w);
+        T* M = ws ? ws + (long long)blockIdx.x * (long long)L.n_max * L.n_max : G;
+        load_transposed(M, A + L.mo(w), n, sm.tile);
+        __syncthreads();
+        gj_invert(M, n, perm, &s_l, &s_s, &s_sing, sm);
+        if (pf) {
+            // the inverse of a skew matrix is skew: keep it exactly so
+            for (long long e = threadIdx.x; e < (long long)n * n; e += RT) {
+                const int i = (int)(e / n), j = (int)(e % n);
+                if (i < j) {
+                    T h = s_half(M[(long long)i * n + j] - M[(long long)j * n + i]);
+                    M[(long long)i * n + j] = h;
+                    M[(long long)j * n + i] = s_neg(h);
+                } else if (i == j) {
+                    M[e] = s_zero(T());
+                }
+            }
+            __syncthreads();
+        }
+        if (ws) {
+            // drift of the tracked inverse, then replace it
+            double num = 0.0, den = 0.0;
+            const int kk = L.kv(w);
+            const int cu = delayed ? S.tau[w] * kk : 0;
+            const long long vo = L.vo(w);
+            for (long long e = threadIdx.x; e < (long long)n * n; e += RT) {
+                const int l = (int)(e / n), j = (int)(e % n);   // memory [l*n + j] = (A^{-1})_{jl}
+                T tr = G[e];
+                if (cu) {
+                    const T* pr = S.P + (vo + j) * L.Kc;
+                    const T* qr = S.Q + (vo + l) * L.Kc;
+                    T s = s_zero(T());
+                    for (int c = 0; c < cu; ++c) s = s_fma(pr[c], qr[c], s);
+                    tr = pf ? tr + s : tr - s;
+                }
+                T f = M[e];
+                num += (double)s_abs2(tr - f);
+                den += (double)s_abs2(f);
+                G[e] = f;
+            }
+            num = warp_sum(num);
+            den = warp_sum(den);
+            if ((threadIdx.x & 31) == 0) { s_red[0][threadIdx.x >> 5] = num; s_red[1][threadIdx.x >> 5] = den; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double a = 0, b = 0;
+                for (int q = 0; q < RT / 32; ++q) { a += s_red[0][q]; b += s_red[1][q]; }
+                if (drift) drift[w] = b > 0 ? sqrt(a / b) : 0.0;
+            }
+        }
+        if (threadIdx.x == 0) {
+            if (write_logdet) {
+                S.logabs[w] = s_l;
+                S.sgn[w] = s_s;
+            }
+            if (delayed) S.tau[w] = 0;
+            S.pst[w] = s_sing ? 1 : 5;   // 5: fresh, no pending proposal
+        }
+        __syncthreads();
+    }
+}
+
+// Pfaffian of a skew n x n matrix (row-major copy in M) by Parlett-Reid
+// elimination with pivoting (see small_pf for the step), one CTA per matrix.
+template <typename T>
+__device__ void pr_pfaffian(T* M, int n, double* logabs, T* sgn, T* s_tau, T* s_row) {
+    __shared__ double s_v[32];
+    __shared__ int s_i[32];
+    __shared__ double s_log;
+    __shared__ T s_sg;
+    __shared__ int s_zero_pf;
+    const int tid = threadIdx.x;
+    if (tid == 0) { s_log = 0.0; s_sg = make_real<T>(1.0); s_zero_pf = (n & 1); }
+    __syncthreads();
+    for (int k = 0; k + 1 < n && !s_zero_pf; k += 2) {
+        double best = -1.0;
+        int bi = -1;
+        for (int i = k + 1 + tid; i < n; i += RT) {
+            double v = (double)s_abs2(M[(long long)i * n + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+        double bv;
+        int p;
+        block_argmax(best, bi, s_v, s_i, bv, p);
+        if (!(bv > 0.0) || p < 0) {
+            if (tid == 0) s_zero_pf = 1;
+            __syncthreads();
+            break;
+        }
+        if (p != k + 1) {
+            // swap rows k+1, p, then columns k+1, p
+            for (int j = tid; j < n; j += RT) {
+                T a = M[(long long)(k + 1) * n + j];
+                M[(long long)(k + 1) * n + j] = M[(long long)p * n + j];
+                M[(long long)p * n + j] = a;
+            }
+            __syncthreads();
+            for (int i = tid; i < n; i += RT) {
+                T a = M[(long long)i * n + k + 1];
+                M[(long long)i * n + k + 1] = M[(long long)i * n + p];
+                M[(long long)i * n + p] = a;
+            }
+        }
+        __syncthreads();
+        const T akk1 = M[(long long)k * n + k + 1];
+        if (tid == 0) {
+            s_log += log(s_absd(akk1));
+            T sg = s_sg * s_unit(akk1);
+            s_sg = (p != k + 1) ? s_neg(sg) : sg;
+        }
+        const T ipiv = s_recip(M[(long long)(k + 1) * n + k]);
+        for (int i = k + 2 + tid; i < n; i += RT) {
+            s_tau[i] = M[(long long)i * n + k] * ipiv;
+            s_row[i] = M[(long long)(k + 1) * n + i];
+        }
+        __syncthreads();
+        const int m = n - k - 2;
+        for (long long e = tid; e < (long long)m * m; e += RT) {
+            const int i = k + 2 + (int)(e / m), j = k + 2 + (int)(e % m);
+            T v = s_fms(s_tau[i], s_row[j], M[(long long)i * n + j]);
+            M[(long long)i * n + j] = s_fma(s_tau[j], s_row[i], v);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        *logabs = s_zero_pf ? -INFINITY : s_log;
+        *sgn = s_zero_pf ? s_zero(T()) : s_renorm(s_sg);
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RT) k_slogpf(DevLayout L, const T* A, const uint8_t* mask, T* ws,
+                                                double* logabs, T* sgn) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    T* s_tau = reinterpret_cast<T*>(dsm);
+    T* s_row = s_tau + 2048;
+    __shared__ double s_l;
+    __shared__ T s_s;
+    for (int w = blockIdx.x; w < L.W; w += gridDim.x) {
+        if (mask && !mask[w]) continue;
+        const int n = L.nw(w);
+        T* M = ws + (long long)blockIdx.x * (long long)L.n_max * L.n_max;
+        const T* Aw = A + L.mo(w);
+        for (long long e = threadIdx.x; e < (long long)n * n; e += RT) M[e] = Aw[e];
+        __syncthreads();
+        pr_pfaffian(M, n, &s_l, &s_s, s_tau, s_row);
+        if (threadIdx.x == 0) {
+            logabs[w] = s_l;
+            sgn[w] = s_s;
+        }
+        __syncthreads();
+    }
+}
+
+// standalone slogdet (GJ on a workspace copy)
+template <typename T>
+__global__ void __launch_bounds__(RT) k_slogdet(int W, int n, const T* A, T* ws, double* logabs, T* sgn) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    GJSmem<T>& sm = *reinterpret_cast<GJSmem<T>*>(dsm);
+    __shared__ int perm[2048];
+    __shared__ double s_l;
+    __shared__ T s_s;
+    __shared__ int s_sing;
+    for (int w = blockIdx.x; w < W; w += gridDim.x) {
+        T* M = ws + (long long)blockIdx.x * n * n;
+        const T* Aw = A + (long long)w * n * n;
+        for (long long e = threadIdx.x; e < (long long)n * n; e += RT) M[e] = Aw[e];
+        __syncthreads();
+        gj_invert(M, n, perm, &s_l, &s_s, &s_sing, sm);
+        if (threadIdx.x == 0) {
+            logabs[w] = s_l;
+            sgn[w] = s_s;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+void launch_refresh(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const T* A,
+                    const uint8_t* mask, T* ws, int nws, double* drift, bool write_logdet, cudaStream_t st) {
+    const int grid = ws ? nws : L.W;
+    const int dyn = (int)sizeof(GJSmem<T>);
+    cudaFuncSetAttribute(k_refresh<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    k_refresh<T><<<grid, RT, dyn, st>>>(L, S, A, mask, ws, nws, drift, pf, delayed, write_logdet);
+}
+
+template <typename T>
+void launch_slogpf(const DevLayout& L, const T* A, const uint8_t* mask, T* ws, int nws, double* logabs, T* sgn,
+                   cudaStream_t st) {
+    const int dyn = (int)(2 * 2048 * sizeof(T));
+    cudaFuncSetAttribute(k_slogpf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    k_slogpf<T><<<nws, RT, dyn, st>>>(L, A, mask, ws, logabs, sgn);
+}
+
+template <typename T>
+void launch_slogdet(int W, int n, const T* A, T* ws, int nws, double* logabs, T* sgn, cudaStream_t st) {
+    const int dyn = (int)sizeof(GJSmem<T>);
+    cudaFuncSetAttribute(k_slogdet<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    k_slogdet<T><<<nws, RT, dyn, st>>>(W, n, A, ws, logabs, sgn);
+}
+
+#define LRU_INST_R(T)                                                                                       \
+    template void launch_refresh<T>(bool, bool, const DevLayout&, const DevState<T>&, const T*,            \
+                                    const uint8_t*, T*, int, double*, bool, cudaStream_t);                 \
+    template void launch_slogpf<T>(const DevLayout&, const T*, const uint8_t*, T*, int, double*, T*,       \
+                                   cudaStream_t);                                                          \
+    template void launch_slogdet<T>(int, int, const T*, T*, int, double*, T*, cudaStream_t);
+
+LRU_INST_R(double)
+LRU_INST_R(float)
+LRU_INST_R(c128)
+LRU_INST_R(c64)
+
+}  // namespace lru

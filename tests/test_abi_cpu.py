@@ -1,0 +1,91 @@
+"""The C-ABI library loads and exports every symbol include/lrugb.h declares.
+
+No GPU needed: only host-side entry points are called (status strings,
+version, argument validation that fails before any CUDA call).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lrugb.h")
+LIB = os.path.join(ROOT, "paper_2602_05255_gb300", "liblrugb.so")
+
+
+def declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:lru_status|const char\*)\s+(lru_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(LIB):
+        import __graft_entry__
+        __graft_entry__.build()
+    return ctypes.CDLL(LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for must in ["lru_create", "lru_init_det", "lru_init_pf", "lru_propose_det", "lru_propose_pf",
+                 "lru_accept", "lru_flush_delayed", "lru_refresh_from_scratch", "lru_get_inverse",
+                 "lru_get_logvalue", "lru_save_state", "lru_load_state"]:
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("lrugb_sig", os.path.join(ROOT, "paper_2602_05255_gb300", "lrugb.py"))
+    src = open(spec.origin).read()
+    for name in declared():
+        assert name in src, name
+
+
+def test_host_only_entry_points(lib):
+    lib.lru_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.lru_version()
+    lib.lru_status_string.restype = ctypes.c_char_p
+    assert lib.lru_status_string(0) == b"ok"
+    assert b"argument" in lib.lru_status_string(1)
+
+
+class Cfg(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("walkers", ctypes.c_int64),
+                ("n", ctypes.c_int32), ("n_per_walker", ctypes.c_void_p), ("k", ctypes.c_int32),
+                ("k_per_walker", ctypes.c_void_p), ("delay", ctypes.c_int32), ("flush", ctypes.c_int32),
+                ("device", ctypes.c_int32)]
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("kind", 7, 1), ("dtype", 9, 1), ("walkers", 0, 1), ("k", 0, 1), ("k", 17, 1),
+    ("delay", -1, 1), ("flush", 11, 1), ("delay", 65, 1),
+])
+def test_create_rejects_bad_config_before_cuda(lib, field, value, code):
+    cfg = Cfg(kind=0, dtype=0, walkers=4, n=16, n_per_walker=None, k=1, k_per_walker=None, delay=0,
+              flush=0, device=0)
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    assert lib.lru_create(ctypes.byref(cfg), ctypes.byref(h)) == code
+    assert not h.value
+
+
+def test_tensor_flush_needs_delayed_f64(lib):
+    cfg = Cfg(kind=0, dtype=1, walkers=4, n=16, n_per_walker=None, k=1, k_per_walker=None, delay=4,
+              flush=1, device=0)
+    h = ctypes.c_void_p()
+    assert lib.lru_create(ctypes.byref(cfg), ctypes.byref(h)) == 8     # UNSUPPORTED, complex
+    cfg.dtype, cfg.delay = 0, 0
+    assert lib.lru_create(ctypes.byref(cfg), ctypes.byref(h)) == 8     # UNSUPPORTED, plain
+
+
+def test_null_arguments(lib):
+    assert lib.lru_create(None, None) == 1
+    assert lib.lru_destroy(None) == 1
+    assert lib.lru_accept(None, None) == 1

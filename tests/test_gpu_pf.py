@@ -1,0 +1,116 @@
+"""GPU parity of the Pfaffian path (Sec. 3, App. A) against the CPU oracle."""
+import numpy as np
+import pytest
+
+from gpu_common import O, RTOL_F64, fro_rel, lrugb, pf_workload, rel, tdev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def run_pf_chain(L, F, pos0, slot, new, delay=0):
+    W, n = pos0.shape
+    dtype = torch.complex128 if np.iscomplexobj(F) else torch.float64
+    st = L.LowRankState("pf", W, n, k=1, dtype=dtype, delay=delay)
+    F_d, pos_d = tdev(F), tdev(pos0)
+    A0 = np.stack([O.pairing_matrix(F, pos0[w]) for w in range(W)])
+    logabs0, sign0 = st.init(tdev(A0))
+    ratios = []
+    for s in range(slot.shape[0]):
+        B, idx = st.form_pf_moves(F_d, pos_d, tdev(slot[s]), tdev(new[s]))
+        r, status = st.propose_pf(L.Operand(dense=B, idx=idx, onehot_mask=0b10))
+        assert (status.cpu().numpy() == 0).all()
+        st.accept()
+        st.commit_moves(pos_d, tdev(slot[s]), tdev(new[s]))
+        ratios.append(r.cpu().numpy())
+    torch.cuda.synchronize()
+    return st, np.array(ratios), pos_d.cpu().numpy(), logabs0.cpu().numpy(), sign0.cpu().numpy()
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("delay", [0, 4])
+def test_row_col_chain_matches_oracle(cplx, delay):
+    # 4 walkers, n = 40 particles on 96 sites, 30 row-and-column moves (Eq. pf_rank2)
+    L = lrugb()
+    W, n, m, steps = 4, 40, 96, 30
+    F, pos0, slot, new = pf_workload(80 + delay, W, n, m, steps, cplx)
+    st, ratios, pos_end, logabs0, sign0 = run_pf_chain(L, F, pos0, slot, new, delay)
+    inv_gpu = st.inverse().cpu().numpy()
+    logabs, sign = (x.cpu().numpy() for x in st.logvalue())
+    for w in range(W):
+        pos = pos0[w].copy()
+        A = O.pairing_matrix(F, pos)
+        s0, l0 = O.slogpf(A)
+        assert abs(logabs0[w] - l0) <= 1e-10 * max(1, abs(l0)) and abs(sign0[w] - s0) <= 1e-10
+        if delay:
+            car = O.init_pf_carrier(A, delay)
+        else:
+            Ainv = O.skew_part(O.inv(A))
+        for s in range(steps):
+            B, C = O.pf_row_col_move(F, pos, slot[s, w], new[s, w])
+            if delay:
+                r = O.pf_lru_delayed(car, B, C)
+            else:
+                r, Ainv = O.pf_lru(Ainv, B, C, return_update=True)
+            assert rel(ratios[s, w], r) <= RTOL_F64, (s, w, ratios[s, w], r)
+            pos[slot[s, w]] = new[s, w]
+        assert np.array_equal(pos, pos_end[w])
+        ref = O.carrier_inverse(car) if delay else Ainv
+        assert fro_rel(inv_gpu[w], ref) <= RTOL_F64
+        A = O.pairing_matrix(F, pos)
+        s1, l1 = O.slogpf(A)
+        assert abs(logabs[w] - l1) <= 1e-9 * max(1, abs(l1))
+        assert abs(sign[w] - s1) <= 1e-8
+        if delay:
+            # A_0^{-1} is kept exactly skew by the mirrored flush
+            assert np.array_equal(inv_gpu[w], -inv_gpu[w].T) or steps % delay != 0
+
+
+@pytest.mark.parametrize("delay", [0, 3])
+def test_general_C_rank2(delay):
+    # k = 2: dense B (n x 4) and a random invertible skew C per walker (App. A.2, Eq. pf_low_rank)
+    L = lrugb()
+    W, n, k, steps = 3, 24, 2, 7
+    g = np.random.Generator(np.random.PCG64(91))
+    A = g.standard_normal((W, n, n))
+    A = A - A.transpose(0, 2, 1)
+    st = L.LowRankState("pf", W, n, k=k, dtype=torch.float64, delay=delay)
+    st.init(tdev(A))
+    cars = [O.init_pf_carrier(A[w], delay) if delay else None for w in range(W)]
+    Ainv = [O.skew_part(O.inv(A[w])) for w in range(W)]
+    for s in range(steps):
+        Bd = g.standard_normal((W, 2 * k, n)) * 0.3
+        Cm = g.standard_normal((W, 2 * k, 2 * k))
+        Cm = Cm - Cm.transpose(0, 2, 1)
+        r, status = st.propose_pf(L.Operand(dense=tdev(Bd)), tdev(Cm))
+        st.accept()
+        r = r.cpu().numpy()
+        for w in range(W):
+            B = Bd[w].T
+            if delay:
+                ref = O.pf_lru_delayed(cars[w], B, Cm[w])
+            else:
+                ref, Ainv[w] = O.pf_lru(Ainv[w], B, Cm[w], return_update=True)
+            assert rel(r[w], ref) <= 1e-9, (s, w, r[w], ref)
+            assert rel(r[w], O.pf_ratio_direct(A[w], B, Cm[w])) <= 1e-8
+            A[w] = A[w] + B @ Cm[w] @ B.T
+    inv_gpu = st.inverse().cpu().numpy()
+    for w in range(W):
+        assert fro_rel(inv_gpu[w], O.inv(A[w])) <= 1e-8
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_slogpf_batched(cplx):
+    L = lrugb()
+    g = np.random.Generator(np.random.PCG64(97))
+    for n in (2, 4, 10, 64, 130):
+        A = g.standard_normal((4, n, n)) + (1j * g.standard_normal((4, n, n)) if cplx else 0)
+        A = A - A.transpose(0, 2, 1)
+        sgn, logabs = L.slogpf_batched(tdev(A))
+        for w in range(4):
+            s_ref, l_ref = O.slogpf(A[w])
+            assert abs(logabs[w].item() - l_ref) <= 1e-10 * max(1, abs(l_ref)), n
+            assert abs(sgn[w].cpu().item() - s_ref) <= 1e-9, n
+    # worked example of App. A.1: pf = af - be + cd
+    M = np.array([[0, 2, 3, 5], [-2, 0, 7, 11], [-3, -7, 0, 13], [-5, -11, -13, 0]], float)[None]
+    sgn, logabs = L.slogpf_batched(tdev(M))
+    assert sgn.item() * np.exp(logabs.item()) == pytest.approx(28.0, rel=1e-14)
