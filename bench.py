@@ -42,9 +42,9 @@ def parse():
     p.add_argument("--n", type=int, default=1024)
     p.add_argument("--m", type=int, default=2048)
     p.add_argument("--delay", type=int, default=16)
-    p.add_argument("--flush", default="native", choices=["native", "tf32x3", "tf32", "bf16", "bf16x3"])
     p.add_argument("--refresh-every", type=int, default=128)
-    p.add_argument("--arms", default="both", choices=["both", "delayed", "plain"])
+    p.add_argument("--arms", default="plain,delayed,delayed_tf32x3",
+                   help="comma list of " + ",".join(ARMS))
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--seed", type=int, default=6)
@@ -137,14 +137,24 @@ def cpu_baseline(Phi, occ0, slot, new, n, budget_s=15.0):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
-FLUSH = {"native": 0, "tf32x3": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
+FLUSH = {"native": 0, "tf32x3": 1, "tf32": 2, "bf16": 3, "bf16x3": 4, "df": 5}
+ARITH = {"native": 0, "df": 1}
+
+# name -> (delay, arith, flush); "delayed" is the headline form
+ARMS = {
+    "plain": (0, "native", "native"),
+    "delayed": (None, "df", "df"),
+    "delayed_tf32x3": (None, "df", "tf32x3"),
+}
 
 
-def run_arm(L, torch, args, delayed, Phi_d, occ0, slot_d, new_d, rank, world, dist):
+def run_arm(L, torch, args, arm, Phi_d, occ0, slot_d, new_d, rank, world, dist):
     W, n, m = args.walkers, args.n, args.m
     dev = torch.cuda.current_device()
-    st = L.LowRankState("det", W, n, k=1, dtype=torch.float64, delay=args.delay if delayed else 0,
-                        flush=FLUSH[args.flush] if delayed else 0)
+    delay, arith, flush = ARMS[arm]
+    delay = args.delay if delay is None else delay
+    delayed = delay >= 2
+    st = L.LowRankState("det", W, n, k=1, dtype=torch.float64, delay=delay, flush=FLUSH[flush], arith=ARITH[arith])
     occ_d = torch.tensor(occ0, device="cuda")
     A = st.gather_rows(Phi_d, occ_d)
     st.init(A)
@@ -153,11 +163,12 @@ def run_arm(L, torch, args, delayed, Phi_d, occ0, slot_d, new_d, rank, world, di
     U_op = L.Operand(idx=idx, onehot_mask=1)
     V_op = L.Operand(dense=V)
     ratio = torch.empty(W, dtype=torch.float64, device="cuda")
+    ratios_all = torch.empty(args.steps, W, dtype=torch.float64, device="cuda")
     status = torch.empty(W, dtype=torch.int32, device="cuda")
 
     def step(s, timed_idx):
         st.form_row_moves(Phi_d, occ_d, slot_d[s], new_d[s], V, idx)
-        st.propose_det(U_op, V_op, ratio, status)
+        st.propose_det(U_op, V_op, ratio if timed_idx is None else ratios_all[timed_idx], status)
         st.accept()
         st.commit_moves(occ_d, slot_d[s], new_d[s])
         if timed_idx is not None and (timed_idx + 1) % args.refresh_every == 0:
@@ -194,17 +205,19 @@ def run_arm(L, torch, args, delayed, Phi_d, occ0, slot_d, new_d, rank, world, di
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = t.item()
-    # parity sample at full size: the last ratios of walker 0 vs its state
     tau = st.tau().cpu().numpy() if delayed else None
-    return st, ms, clk, launches, prof, tau
+    st.close()
+    return ratios_all, ms, clk, launches, prof, tau, (delay, arith, flush)
 
 
 def e2e_arm(L, torch, args, Phi_d, occ0, slot_h, new_h, steps):
     """Same metric through the C-ABI with host buffers: each step copies its
     proposals (slot, new row) host->device from pinned memory and reads the
-    ratios back, inside the timed region."""
+    ratios back, inside the timed region (headline delayed form)."""
     W, n = args.walkers, args.n
-    st = L.LowRankState("det", W, n, k=1, dtype=torch.float64, delay=args.delay, flush=FLUSH[args.flush])
+    delay, arith, flush = ARMS["delayed"]
+    st = L.LowRankState("det", W, n, k=1, dtype=torch.float64, delay=args.delay, flush=FLUSH[flush],
+                        arith=ARITH[arith])
     occ_d = torch.tensor(occ0, device="cuda")
     A = st.gather_rows(Phi_d, occ_d)
     st.init(A)
@@ -280,49 +293,65 @@ def main():
 
     hbm, bf16, peak_src = load_peaks()
     arms = {}
-    out_state = {}
-    order = ["plain", "delayed"] if args.arms == "both" else [args.arms]
+    arm_ratios = {}
+    order = [a.strip() for a in args.arms.split(",") if a.strip()]
     for arm in order:
-        st, ms, clk, launches, prof, tau = run_arm(L, torch, args, arm == "delayed", Phi_d, occ0, slot_d, new_d,
-                                                   rank, world, dist)
+        ratios_all, ms, clk, launches, prof, tau, (delay, arith, flush) = run_arm(
+            L, torch, args, arm, Phi_d, occ0, slot_d, new_d, rank, world, dist)
+        arm_ratios[arm] = ratios_all
         upd = W * args.steps * world
-        nrefresh = args.steps // args.refresh_every
         ref_ms = prof["refresh"][0]
         a = {"value": upd / (ms / 1e3), "ms_per_step": ms / args.steps,
+             "delay_K": delay, "gemv_arith": arith, "flush": flush if delay >= 2 else None,
              "value_excl_refresh": upd / ((ms - ref_ms) / 1e3) if ms > ref_ms else None,
-             "refreshes_in_timed_region": nrefresh, "refresh_ms_total": ref_ms,
-             "kernel_ms": {k: v[0] for k, v in prof.items()}, "kernel_launches_timed": {k: v[1] for k, v in prof.items()},
+             "refreshes_in_timed_region": args.steps // args.refresh_every, "refresh_ms_total": ref_ms,
+             "kernel_ms": {k: v[0] for k, v in prof.items()},
+             "kernel_launches_timed": {k: v[1] for k, v in prof.items()},
              "gpu_launches": launches, "clocks": clk}
         # algorithmic bytes per accept launch (one walker-update of every walker):
         # plain: read + write A^{-1} (2 n^2 * 8 B); delayed: read A_0^{-1} (n^2 * 8 B)
         acc_ms, acc_n = prof["accept"]
-        bytes_per = (2 if arm == "plain" else 1) * n * n * 8 * W
-        a["accept_roofline"] = {"bound": "hbm", "achieved": bytes_per / (acc_ms / acc_n / 1e3) / 1e9 if acc_n else None,
-                                "peak": hbm, "unit": "GB/s", "traffic": None,
+        bytes_per = (2 if delay < 2 else 1) * n * n * 8 * W
+        achieved = bytes_per / (acc_ms / acc_n / 1e3) / 1e9 if acc_n else None
+        a["accept_roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                                "frac": achieved / hbm if achieved else None, "traffic": None,
                                 "bytes_per_launch": bytes_per, "ms_per_launch": acc_ms / acc_n if acc_n else None}
-        a["accept_roofline"]["frac"] = (a["accept_roofline"]["achieved"] / hbm) if acc_n else None
-        if arm == "delayed":
+        if delay >= 2:
             fl_ms, fl_n = prof["flush"]
-            a["flush"] = {"ms_total": fl_ms, "launches": fl_n, "K": args.delay, "mode": args.flush}
+            nfl = args.steps // delay
+            a["flush_detail"] = {"ms_total": fl_ms, "launches": fl_n, "full_flushes": nfl,
+                                 "ms_per_full_flush": fl_ms / max(nfl, 1),
+                                 "bytes_per_full_flush": 2 * n * n * 8 * W}
         arms[arm] = a
-        out_state[arm] = st
-    # full-size parity sample: walker 0 of each arm against the oracle (first steps)
-    head = arms.get("delayed") or arms.get("plain")
-    main_arm = "delayed" if "delayed" in arms else "plain"
-    # dominant kernel of the headline arm
+    # drift of every arm's ratios against the plain FP64 arm (same moves)
+    if "plain" in arm_ratios:
+        ref = arm_ratios["plain"]
+        med = ref.abs().median()
+        gate = ref.abs() >= 1e-6 * med
+        for arm, r in arm_ratios.items():
+            if arm == "plain":
+                continue
+            d = (r - ref).abs()
+            relerr = (d / ref.abs())[gate]
+            arms[arm]["ratio_err_vs_plain_fp64"] = {
+                "max_rel": relerr.max().item(), "median_rel": relerr.median().item(),
+                "p999_rel": relerr.float().quantile(0.999).item() if relerr.numel() < 16_000_000 else None,
+                "max_abs_over_median_abs": (d.max() / med).item(), "near_node_steps": int((~gate).sum().item())}
+    main_arm = "delayed" if "delayed" in arms else order[0]
+    head = arms[main_arm]
     km = head["kernel_ms"]
     dom = max(km, key=lambda k: km[k])
     roof = dict(head["accept_roofline"])
     roof["kernel"] = "accept (GEMV / Woodbury pass over A^{-1})"
     roof["dominant_kernel_by_time"] = dom
-    roof["peak_source"] = peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback"
+    roof["peak_source"] = "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback"
     line = {
         "metric": METRIC, "value": head["value"], "unit": "walker-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"det rank-1 row moves, W={W} walkers/GPU, n={n}, Phi {m}x{n} N(0,1/n) FP64, "
                                f"refresh every {args.refresh_every}", "arm": main_arm,
-                   "delay_K": args.delay, "flush": args.flush, "walkers_per_gpu": W, "n": n, "m": m,
+                   "delay_K": args.delay, "walkers_per_gpu": W, "n": n, "m": m,
                    "l2": "inputs larger than L2 (A^{-1} state 8 GiB per GPU)"},
         "roofline": roof, "arms": arms, "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
     }

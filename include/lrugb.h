@@ -77,8 +77,16 @@ typedef enum {
     LRU_FLUSH_TF32X3 = 1,   /* tcgen05 TF32 tensor cores, 3-term split (about FP32 accuracy) */
     LRU_FLUSH_TF32 = 2,     /* tcgen05 TF32, one term */
     LRU_FLUSH_BF16 = 3,     /* tcgen05 BF16, one term */
-    LRU_FLUSH_BF16X3 = 4    /* tcgen05 BF16, 3-term split */
+    LRU_FLUSH_BF16X3 = 4,   /* tcgen05 BF16, 3-term split */
+    LRU_FLUSH_DF = 5        /* F64 only: double-float products on the FP32 pipe (about 1e-14 relative) */
 } lru_flush;
+
+/* Arithmetic of the streaming passes over A^{-1} for F64 handles. */
+typedef enum {
+    LRU_ARITH_NATIVE = 0,   /* FP64 FMAs */
+    LRU_ARITH_DF = 1        /* double-float (pairs of FP32) from integer-split FP64 data; the
+                               delayed GEMV of rank-1 determinant updates uses it */
+} lru_arith;
 
 typedef struct {
     int32_t kind;                 /* lru_kind */
@@ -91,6 +99,7 @@ typedef struct {
     int32_t delay;                /* K of the delayed form (Sec. 2.3 / 3.3); 0 or 1 = plain updates */
     int32_t flush;                /* lru_flush */
     int32_t device;               /* CUDA device ordinal */
+    int32_t arith;                /* lru_arith (F64 handles; ignored otherwise) */
 } lru_config;
 
 /* One operand of a proposal: kmax vector slots per walker (see Conventions).

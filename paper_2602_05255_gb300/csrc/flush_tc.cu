@@ -1,14 +1,364 @@
-// Tensor-core delayed flush (placeholder until the tcgen05 kernel lands).
+// Delayed flush on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// The delayed forms keep A_0^{-1} and K correction slots and fold them every K
+// accepted steps (Sec. 2.3 Eq. delayed_Ainv: A^{-1} = A_0^{-1} - P Q^T; Sec.
+// 3.3 Eq. pf_delayed_Ainv: A^{-1} = A_0^{-1} + P Q^T).  The contraction P Q^T
+// has inner dimension K*k (16..64): it is tiny for the tensor cores, and the
+// cost is the FP64 read-modify-write of A_0^{-1}.  The kernel therefore
+// streams 128 x 128 output tiles through one persistent CTA per SM slot:
+//   TMA (SWIZZLE_128B, no multicast) brings the TF32 hi/lo splits of the P and
+//   Q rows of the tile into shared memory; one thread issues the MMAs
+//   (3 terms hi*hi + hi*lo + lo*hi for FP32-class accuracy, or 1 term) into a
+//   128 x 128 FP32 accumulator in tensor memory; all eight warps read it back
+//   with tcgen05.ld and update the FP64 tile in global memory (coalesced
+//   256-byte rows, float->double by integer ops so only the final add uses the
+//   slow FP64 pipe).  For the Pfaffian only tiles with J <= L are computed and
+//   the mirror tile is written as the exact negative transpose, keeping
+//   A_0^{-1} exactly skew.
+// Every wait on an mbarrier is bounded; on time-out the kernel records
+// DEV_ERR_TIMEOUT, waits (bounded) for its copies in flight, frees its tensor
+// memory and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
 #include "internal.h"
 
 namespace lru {
 
+constexpr int TC_THREADS = 256;
+constexpr int TILE = 128;         // M = N = 128
+constexpr int KCHUNK = 32;        // TF32 elements per 128-byte swizzle row
+constexpr int CHUNK_BYTES = TILE * KCHUNK * 4;   // 16 KiB per operand per K chunk
+constexpr uint32_t TMEM_COLS = 128;
+
+struct TcMaps {
+    CUtensorMap ph, pl, qh, ql;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: about a second at most
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+    for (int i = 0; i < (1 << 20); ++i) {
+        if (mbar_try(a, parity)) return true;
+        if (i > 64) __nanosleep(256);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, SWIZZLE_128B, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
+    d |= (uint64_t)2 << 61;                          // SWIZZLE_128B
+    return d;
+}
+
+// instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, M = N = 128
+constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TILE >> 3) << 17) |
+                                ((uint32_t)(TILE >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(dtmem), "l"(a), "l"(b), "r"(IDESC_TF32), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// exact float -> double with integer operations (FP32 zeros and subnormals
+// become signed zero; the flush values are far from that range)
+__device__ __forceinline__ double f2d_int(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t mag = u & 0x7FFFFFFFu;
+    uint32_t hi = ((mag >> 3) + 0x38000000u) | (u & 0x80000000u);
+    uint32_t lo = u << 29;
+    if (mag < 0x00800000u) { hi = u & 0x80000000u; lo = 0u; }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// One CTA per SM slot, persistent over the (walker, tile) list of the walkers
+// that flush now.  Walker w flushes when tau_w >= K (or force[w] and tau_w > 0).
+template <bool PF>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_flush_tc(const __grid_constant__ TcMaps maps, DevLayout L, double* G, const int* tau, const uint8_t* force,
+               int nkc, int three, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // 1024-byte aligned operand area: [Ph | Pl | Qh | Ql] x nkc chunks
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sPh = sm;
+    unsigned char* sPl = sPh + nkc * CHUNK_BYTES;
+    unsigned char* sQh = sPl + nkc * CHUNK_BYTES;
+    unsigned char* sQl = sQh + nkc * CHUNK_BYTES;
+    // mirror staging (pf): one 32 x 33 block per warp (warps q and q+4 share TMEM lanes)
+    double* sT = reinterpret_cast<double*>(sQl + nkc * CHUNK_BYTES) + (size_t)warp * 32 * 33;
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const uint32_t mb_tma = smem_u32(&mbar[0]), mb_mma = smem_u32(&mbar[1]);
+    const uint32_t tx_bytes = 4u * nkc * CHUNK_BYTES;
+
+    uint32_t phase = 0;
+    long long offset = 0;   // running index over the concatenated tile list
+    for (int w = 0; w < L.W && !s_abort; ++w) {
+        const int t = tau[w];
+        const bool go = force ? (force[w] && t > 0) : (t >= L.K);
+        if (!go) continue;
+        const int n = L.nw(w);
+        const int nt = (n + TILE - 1) / TILE;
+        const int ntiles = PF ? nt * (nt + 1) / 2 : nt * nt;
+        const long long vo = L.vo(w);
+        double* Gw = G + L.mo(w);
+        // tiles of this walker owned by this CTA
+        long long first = ((long long)blockIdx.x - offset) % gridDim.x;
+        if (first < 0) first += gridDim.x;
+        for (long long ti = first; ti < ntiles; ti += gridDim.x) {
+            int tJ, tL;
+            if (PF) {
+                // row-major enumeration of the upper triangle J <= L
+                int r = 0, rem = (int)ti;
+                while (rem >= nt - r) { rem -= nt - r; ++r; }
+                tJ = r;
+                tL = r + rem;
+            } else {
+                tJ = (int)(ti % nt);
+                tL = (int)(ti / nt);
+            }
+            const int j0 = tJ * TILE, l0 = tL * TILE;
+            // ---- TMA: P rows j0.. and Q rows l0.. of this walker ----
+            if (tid == 0) {
+                mbar_expect_tx(mb_tma, tx_bytes);
+                for (int kc = 0; kc < nkc; ++kc) {
+                    tma_load_2d(smem_u32(sPh + kc * CHUNK_BYTES), &maps.ph, kc * KCHUNK, (int)(vo + j0), mb_tma);
+                    tma_load_2d(smem_u32(sPl + kc * CHUNK_BYTES), &maps.pl, kc * KCHUNK, (int)(vo + j0), mb_tma);
+                    tma_load_2d(smem_u32(sQh + kc * CHUNK_BYTES), &maps.qh, kc * KCHUNK, (int)(vo + l0), mb_tma);
+                    tma_load_2d(smem_u32(sQl + kc * CHUNK_BYTES), &maps.ql, kc * KCHUNK, (int)(vo + l0), mb_tma);
+                }
+                if (!mbar_wait(mb_tma, phase)) {
+                    set_dev_error(err, DEV_ERR_TIMEOUT);
+                    s_abort = 1;
+                    mbar_wait(mb_tma, phase);   // let copies in flight land before leaving
+                } else {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    // ---- MMA: D = sum_k P_k Q_k^T (hi*hi [+ hi*lo + lo*hi]) ----
+                    uint32_t acc = 0;
+                    for (int kc = 0; kc < nkc; ++kc) {
+                        const uint64_t ah = desc_sw128(smem_u32(sPh + kc * CHUNK_BYTES));
+                        const uint64_t al = desc_sw128(smem_u32(sPl + kc * CHUNK_BYTES));
+                        const uint64_t bh = desc_sw128(smem_u32(sQh + kc * CHUNK_BYTES));
+                        const uint64_t bl = desc_sw128(smem_u32(sQl + kc * CHUNK_BYTES));
+#pragma unroll
+                        for (int ks = 0; ks < KCHUNK / 8; ++ks) {
+                            const uint64_t adv = (uint64_t)(ks * 32) >> 4;   // 8 TF32 = 32 bytes along K
+                            if (three) {
+                                mma_tf32(tmem, al + adv, bh + adv, acc);
+                                acc = 1;
+                                mma_tf32(tmem, ah + adv, bl + adv, 1);
+                            }
+                            mma_tf32(tmem, ah + adv, bh + adv, acc);
+                            acc = 1;
+                        }
+                    }
+                    mma_commit(mb_mma);
+                }
+            }
+            __syncthreads();
+            if (s_abort) break;
+            // ---- wait for the accumulator ----
+            bool ok = mbar_wait(mb_mma, phase);
+            if (!ok) {
+                set_dev_error(err, DEV_ERR_TIMEOUT);
+                s_abort = 1;
+            }
+            __syncthreads();
+            if (s_abort) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            phase ^= 1u;
+            // ---- epilogue: warp q reads TMEM lanes 32 (q % 4) .. +31 (rows j),
+            //      warpgroup q / 4 takes columns 64 (q / 4) .. +63 ----
+            const int quad = warp & 3, half = warp >> 2;
+            const int jl = 32 * quad + lane;
+            const int j = j0 + jl;
+            for (int ch = 0; ch < 2; ++ch) {
+                const int c0 = 64 * half + 32 * ch;
+                float acc[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, acc);
+                double g[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int l = l0 + c0 + c;
+                    const bool keep = j < n && l < n && (!PF || tJ != tL || j < l);
+                    g[c] = keep ? Gw[(long long)l * n + j] : 0.0;
+                }
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int l = l0 + c0 + c;
+                    const double d = f2d_int(acc[c]);
+                    const double nv = PF ? g[c] + d : g[c] - d;
+                    if (j < n && l < n) {
+                        if (!PF || tJ != tL || j < l) Gw[(long long)l * n + j] = nv;
+                        else if (j == l) Gw[(long long)l * n + j] = 0.0;
+                    }
+                    if (PF) sT[lane * 33 + c] = nv;
+                }
+                if (PF) {
+                    __syncwarp();
+                    // mirror: (l, j) = -(j, l) at G[j*n + l], 32 consecutive l per row j
+#pragma unroll 4
+                    for (int r = 0; r < 32; ++r) {
+                        const int jr = j0 + 32 * quad + r;
+                        const int l = l0 + c0 + lane;
+                        if (jr < n && l < n && (tJ != tL || jr < l))
+                            Gw[(long long)jr * n + l] = -sT[r * 33 + lane];
+                    }
+                    __syncwarp();
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+        offset += ntiles;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---- host side ----------------------------------------------------------------
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled get_encode() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiled)p;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// rows x cols float matrix (row-major, cols = Kc_pad), box 32 x 128, SWIZZLE_128B
+static bool make_map(CUtensorMap* m, const float* base, long long rows, int cols) {
+    EncodeTiled enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)TILE};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 bool launch_flush_tc(int mode, bool pf, const DevLayout& L, double* G, const float* Ph, const float* Pl,
                      const float* Qh, const float* Ql, const int* tau, const uint8_t* force_mask, int* err,
                      cudaStream_t st) {
-    (void)mode; (void)pf; (void)L; (void)G; (void)Ph; (void)Pl; (void)Qh; (void)Ql; (void)tau;
-    (void)force_mask; (void)err; (void)st;
-    return false;
+    // mode: 1 = TF32x3, 2 = TF32 (BF16 modes are not built)
+    if (mode != 1 && mode != 2) return false;
+    if (L.Kc32 <= 0 || L.Kc32 % KCHUNK) return false;
+    static thread_local const float* cached[4] = {nullptr, nullptr, nullptr, nullptr};
+    static thread_local long long cached_rows = -1;
+    static thread_local int cached_cols = -1;
+    static thread_local TcMaps maps;
+    if (cached[0] != Ph || cached[1] != Pl || cached[2] != Qh || cached[3] != Ql || cached_rows != L.rows ||
+        cached_cols != L.Kc32) {
+        if (!make_map(&maps.ph, Ph, L.rows, L.Kc32) || !make_map(&maps.pl, Pl, L.rows, L.Kc32) ||
+            !make_map(&maps.qh, Qh, L.rows, L.Kc32) || !make_map(&maps.ql, Ql, L.rows, L.Kc32))
+            return false;
+        cached[0] = Ph; cached[1] = Pl; cached[2] = Qh; cached[3] = Ql;
+        cached_rows = L.rows;
+        cached_cols = L.Kc32;
+    }
+    const int nkc = L.Kc32 / KCHUNK;
+    const size_t dyn = 1024 + (size_t)4 * nkc * CHUNK_BYTES + (pf ? (size_t)8 * 32 * 33 * sizeof(double) : 0);
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    auto kern = pf ? k_flush_tc<true> : k_flush_tc<false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    kern<<<nsm, TC_THREADS, dyn, st>>>(maps, L, G, tau, force_mask, nkc, mode == 1 ? 1 : 0, err);
+    return true;
 }
 
 }  // namespace lru

@@ -20,6 +20,8 @@ struct DevLayout {
     const int* kvec;           // per-walker vector count, or nullptr (= kk)
     int Kc;                    // delay columns per walker row of P, Q (K * kk), 0 if plain
     int K;                     // delay length (>= 2 for the delayed form)
+    int Kc32;                  // row stride of the FP32 split copies (Kc rounded up to 32)
+    long long rows;            // sum of n over walkers (rows of P, Q)
     __device__ __forceinline__ int nw(int w) const { return n_uni > 0 ? n_uni : n[w]; }
     __device__ __forceinline__ long long mo(int w) const {
         return n_uni > 0 ? (long long)w * n_uni * n_uni : moff[w];
@@ -65,11 +67,13 @@ template <typename T>
 void launch_propose(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& U,
                     const DevOperand& V, const T* C, T* ratio_out, int* st_out, cudaStream_t st);
 template <typename T>
-void launch_accept(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
+void launch_accept(bool pf, bool delayed, bool df, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
                    const uint8_t* mask, const int* items, int nitems, cudaStream_t st);
 template <typename T>
 void launch_flush_native(bool pf, const DevLayout& L, const DevState<T>& S, const uint8_t* force_mask,
                          int nwalkers_tiles, cudaStream_t st);
+void launch_flush_df(bool pf, const DevLayout& L, const DevState<double>& S, const uint8_t* force_mask,
+                     cudaStream_t st);
 template <typename T>
 void launch_flush_finish(const DevLayout& L, const DevState<T>& S, const uint8_t* force_mask, cudaStream_t st);
 template <typename T>
@@ -83,6 +87,8 @@ void launch_form_pf_moves(const DevLayout& L, const T* F, int m, const int* pos,
 template <typename T>
 void launch_gather(bool pairs, const DevLayout& L, const T* src, int m, const int* occ, T* A, int* err,
                    cudaStream_t st);
+template <typename T>
+void launch_zero_split_tail(const DevLayout& L, const DevState<T>& S, const uint8_t* force, cudaStream_t st);
 void launch_commit_moves(int W, int n, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
                          const int* pst, cudaStream_t st);
 template <typename T>

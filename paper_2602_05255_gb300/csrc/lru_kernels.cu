@@ -8,8 +8,10 @@
 #include "common.cuh"
 #include "internal.h"
 #include "small_core.cuh"
+#include "df.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace lru {
 
@@ -223,10 +225,11 @@ __global__ void __launch_bounds__(PT) k_propose(DevLayout L, DevState<T> S, DevO
                     S.P[off] = x;
                     if constexpr (!traits<T>::is_complex && sizeof(T) == 8) {
                         if (S.P32h) {
+                            const long long o32 = (vo + j) * L.Kc32 + cu + a;
                             float h, lo;
                             split_tf32((double)x, h, lo);
-                            S.P32h[off] = h;
-                            S.P32l[off] = lo;
+                            S.P32h[o32] = h;
+                            S.P32l[o32] = lo;
                         }
                     }
                 }
@@ -280,22 +283,34 @@ __global__ void __launch_bounds__(PT) k_propose(DevLayout L, DevState<T> S, DevO
                 for (int j = 0; j < kk; ++j) s_inv[i * MAXKK + j] = s_core[i * MAXKK + j];
             st = small_gj_inverse(s_inv, kk, MAXKK, &ratio);
         } else {
-            // M is skew in exact arithmetic: keep it exactly skew
+            // The plain path applies the generic Woodbury form and needs the
+            // inverse of M exactly as computed: projecting M onto its skew part
+            // there makes the chain unstable.  The delayed path uses the skew
+            // form (Eq. pf_delayed_Ainv), which needs M and M^{-1} exactly skew.
+            if (DELAYED)
+                for (int i = 0; i < kk; ++i)
+                    for (int j = i; j < kk; ++j) {
+                        T h = s_half(s_core[i * MAXKK + j] - s_core[j * MAXKK + i]);
+                        s_core[i * MAXKK + j] = h;
+                        s_core[j * MAXKK + i] = s_neg(h);
+                    }
+            for (int i = 0; i < kk; ++i)
+                for (int j = 0; j < kk; ++j) s_inv[i * MAXKK + j] = s_core[i * MAXKK + j];
+            T dM;
+            st = small_gj_inverse(s_inv, kk, MAXKK, &dM);
+            if (DELAYED)
+                for (int i = 0; i < kk; ++i)
+                    for (int j = i; j < kk; ++j) {
+                        T h = s_half(s_inv[i * MAXKK + j] - s_inv[j * MAXKK + i]);
+                        s_inv[i * MAXKK + j] = h;
+                        s_inv[j * MAXKK + i] = s_neg(h);
+                    }
+            // pf of the skew part of M (the ratio, Eq. pf_low_rank)
             for (int i = 0; i < kk; ++i)
                 for (int j = i; j < kk; ++j) {
                     T h = s_half(s_core[i * MAXKK + j] - s_core[j * MAXKK + i]);
                     s_core[i * MAXKK + j] = h;
                     s_core[j * MAXKK + i] = s_neg(h);
-                }
-            for (int i = 0; i < kk; ++i)
-                for (int j = 0; j < kk; ++j) s_inv[i * MAXKK + j] = s_core[i * MAXKK + j];
-            T dM;
-            st = small_gj_inverse(s_inv, kk, MAXKK, &dM);
-            for (int i = 0; i < kk; ++i)
-                for (int j = i; j < kk; ++j) {
-                    T h = s_half(s_inv[i * MAXKK + j] - s_inv[j * MAXKK + i]);
-                    s_inv[i * MAXKK + j] = h;
-                    s_inv[j * MAXKK + i] = s_neg(h);
                 }
             T pfM = small_pf(s_core, kk, MAXKK);
             ratio = pfM * s_recip(s_pfc);
@@ -323,13 +338,14 @@ __global__ void __launch_bounds__(PT) k_propose(DevLayout L, DevState<T> S, DevO
                 S.P[off] = p;
                 if constexpr (!traits<T>::is_complex && sizeof(T) == 8) {
                     if (S.P32h) {
+                        const long long o32 = (vo + j) * L.Kc32 + cu + b;
                         float h, lo;
                         split_tf32((double)p, h, lo);
-                        S.P32h[off] = h;
-                        S.P32l[off] = lo;
+                        S.P32h[o32] = h;
+                        S.P32l[o32] = lo;
                         split_tf32((double)q, h, lo);
-                        S.Q32h[off] = h;
-                        S.Q32l[off] = lo;
+                        S.Q32h[o32] = h;
+                        S.Q32l[o32] = lo;
                     }
                 }
             }
@@ -374,7 +390,7 @@ __global__ void __launch_bounds__(PT) k_qtu_dense(DevLayout L, DevState<T> S, De
 //            generic Woodbury A^{-1} - X M^{-1} (B^T A^{-1}))
 //   delayed: y -= (V P) Q[l,:]^T ; Q[l, tau] = (R^{-1} y)^T     (b_tau equation)
 // ---------------------------------------------------------------------------
-template <typename T, bool DELAYED, int NPL>
+template <typename T, bool DELAYED, int NPL, int KKS>
 __global__ void __launch_bounds__(PT) k_accept(DevLayout L, DevState<T> S, DevOperand V, const uint8_t* mask,
                                                 const int4* items) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -382,7 +398,8 @@ __global__ void __launch_bounds__(PT) k_accept(DevLayout L, DevState<T> S, DevOp
     const int w = it.x;
     if (mask && !mask[w]) return;
     if (S.pst[w] != 0) return;
-    const int n = L.nw(w), kk = L.kv(w);
+    // KKS > 0: the rank is a compile-time constant (register arrays), else runtime
+    const int n = L.nw(w), kk = KKS > 0 ? KKS : L.kv(w);
     const long long vo = L.vo(w);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // X and the dense V vectors are staged in shared memory when they fit
@@ -427,8 +444,9 @@ __global__ void __launch_bounds__(PT) k_accept(DevLayout L, DevState<T> S, DevOp
             const int j = lane + 32 * m;
             v[m] = (j < n) ? col[j] : s_zero(T());
         }
-        T y[MAXKK];
-        for (int b = 0; b < kk; ++b) {
+        T y[KKS > 0 ? KKS : MAXKK];
+#pragma unroll
+        for (int b = 0; b < (KKS > 0 ? KKS : kk); ++b) {
             if (siv[b] >= 0) {
                 y[b] = col[siv[b]];
             } else {
@@ -448,10 +466,12 @@ __global__ void __launch_bounds__(PT) k_accept(DevLayout L, DevState<T> S, DevOp
                 y[b] = y[b] - corr;
             }
         }
-        T z[MAXKK];
-        for (int a = 0; a < kk; ++a) {
+        T z[KKS > 0 ? KKS : MAXKK];
+#pragma unroll
+        for (int a = 0; a < (KKS > 0 ? KKS : kk); ++a) {
             T s = s_zero(T());
-            for (int b = 0; b < kk; ++b) s = s_fma(sR[a * MAXKK + b], y[b], s);
+#pragma unroll
+            for (int b = 0; b < (KKS > 0 ? KKS : kk); ++b) s = s_fma(sR[a * MAXKK + b], y[b], s);
             z[a] = s;
         }
         if constexpr (!DELAYED) {
@@ -460,29 +480,188 @@ __global__ void __launch_bounds__(PT) k_accept(DevLayout L, DevState<T> S, DevOp
                 const int j = lane + 32 * m;
                 if (j < n) {
                     T d = v[m];
-                    for (int a = 0; a < kk; ++a) d = s_fms(sX[(size_t)a * n + j], z[a], d);
+#pragma unroll
+                    for (int a = 0; a < (KKS > 0 ? KKS : kk); ++a) d = s_fms(sX[(size_t)a * n + j], z[a], d);
                     col[j] = d;
                 }
             }
         } else {
             if (lane < kk) {
                 T zz = z[0];
-                for (int a = 1; a < kk; ++a)
+#pragma unroll
+                for (int a = 1; a < (KKS > 0 ? KKS : kk); ++a)
                     if (a == lane) zz = z[a];
                 const long long off = (vo + l) * Kc + cu + lane;
                 S.Q[off] = zz;
                 if constexpr (!traits<T>::is_complex && sizeof(T) == 8) {
                     if (S.P32h) {
+                        const long long o32 = (vo + l) * L.Kc32 + cu + lane;
                         float h, lo;
                         split_tf32((double)zz, h, lo);
-                        S.Q32h[off] = h;
-                        S.Q32l[off] = lo;
+                        S.Q32h[o32] = h;
+                        S.Q32l[o32] = lo;
                     }
                 }
             }
         }
     }
 }
+
+// Delayed accept of a real rank-1 update with the GEMV in double-float
+// arithmetic (FP32 pipe): per chunk l, y = V . chunk_l accumulated as hi+lo
+// floats from integer-split doubles, then in FP64 y -= (V P) Q[l,:]^T and
+// Q[l, tau] = y / r (b_tau equation of Sec. 2.3).  Reads A_0^{-1} once.
+template <int NPL>
+__global__ void __launch_bounds__(PT) k_accept_delayed_df(DevLayout L, DevState<double> S, DevOperand V,
+                                                           const uint8_t* mask, const int4* items) {
+    __shared__ float sVh[2048], sVl[2048];
+    __shared__ double sVP[64];
+    const int4 it = items[blockIdx.x];
+    const int w = it.x;
+    if (mask && !mask[w]) return;
+    if (S.pst[w] != 0) return;
+    const int n = L.nw(w);
+    const long long vo = L.vo(w);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int Kc = L.Kc, cu = S.tau[w];
+    const double* vb = vec_ptr<double>(V, L, w, 0, n);
+    for (int j = threadIdx.x; j < n; j += PT) split_d(vb[j], sVh[j], sVl[j]);
+    for (int c = threadIdx.x; c < cu; c += PT) sVP[c] = S.VP[(long long)w * MAXKK * Kc + c];
+    const double rinv = S.Rinv[(long long)w * MAXKK * MAXKK];
+    __syncthreads();
+    const double* Gw = S.G + L.mo(w);
+    for (int l = it.y + wid; l < it.z; l += PT / 32) {
+        const double* col = Gw + (long long)l * n;
+        double g[NPL];
+#pragma unroll
+        for (int m = 0; m < NPL; ++m) {
+            const int j = lane + 32 * m;
+            g[m] = (j < n) ? col[j] : 0.0;
+        }
+        float ah = 0.f, al = 0.f;
+#pragma unroll
+        for (int m = 0; m < NPL; ++m) {
+            const int j = lane + 32 * m;
+            if (j < n) {
+                float gh, gl;
+                split_d(g[m], gh, gl);
+                df_fma(ah, al, sVh[j], sVl[j], gh, gl);
+            }
+        }
+        df_warp_sum(ah, al);
+        if (lane == 0) {
+            double y = df_to_double(ah, al);
+            const double* qrow = S.Q + (vo + l) * Kc;
+            for (int c = 0; c < cu; ++c) y = fma(-sVP[c], qrow[c], y);
+            const double z = rinv * y;
+            const long long off = (vo + l) * Kc + cu;
+            S.Q[off] = z;
+            if (S.P32h) {
+                const long long o32 = (vo + l) * L.Kc32 + cu;
+                float h, lo;
+                split_tf32(z, h, lo);
+                S.Q32h[o32] = h;
+                S.Q32l[o32] = lo;
+            }
+        }
+    }
+}
+
+#if !defined(LRU_INST_DTYPE) || defined(LRU_INST_PRIMARY)
+// Double-float flush: A_0^{-1} -/+= P Q^T with the Kc-term dot products in
+// hi+lo float arithmetic (relative error ~1e-14, FP32 pipe) and one FP64
+// subtraction per element.  Same tiling and skew mirror as k_flush_native.
+struct DfFlushSmem {
+    float sPh[32][65], sPl[32][65], sQh[32][65], sQl[32][65];
+    double sT[32][33];
+};
+
+template <bool PF>
+__device__ void flush_df_tile(const DevLayout& L, const DevState<double>& S, int w, int tau, int tJ, int tL,
+                              DfFlushSmem& sm) {
+    auto& sPh = sm.sPh;
+    auto& sPl = sm.sPl;
+    auto& sQh = sm.sQh;
+    auto& sQl = sm.sQl;
+    auto& sT = sm.sT;
+    const int n = L.nw(w), kk = L.kv(w);
+    const int cu = tau * kk, Kc = L.Kc;
+    const long long vo = L.vo(w);
+    double* Gw = S.G + L.mo(w);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int j0 = tJ * 32, l0 = tL * 32;
+    for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+        const int r = e / 64, c = e % 64;
+        const bool okc = c < cu;
+        double p = (okc && j0 + r < n) ? S.P[(vo + j0 + r) * Kc + c] : 0.0;
+        double q = (okc && l0 + r < n) ? S.Q[(vo + l0 + r) * Kc + c] : 0.0;
+        split_d(p, sPh[r][c], sPl[r][c]);
+        split_d(q, sQh[r][c], sQl[r][c]);
+    }
+    __syncthreads();
+    float ah[4], al[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { ah[q] = 0.f; al[q] = 0.f; }
+    for (int c = 0; c < cu; ++c) {
+        const float ph = sPh[tx][c], pl = sPl[tx][c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) df_fma(ah[q], al[q], ph, pl, sQh[ty + 8 * q][c], sQl[ty + 8 * q][c]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = j0 + tx, l = l0 + ty + 8 * q;
+        double nv = 0.0;
+        if (j < n && l < n) {
+            const double g = Gw[(long long)l * n + j];
+            const double dh = f2d_int(ah[q]), dl = f2d_int(al[q]);
+            nv = PF ? (g + dh) + dl : (g - dh) - dl;
+        }
+        sT[ty + 8 * q][tx] = nv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = j0 + tx, l = l0 + ty + 8 * q;
+        if (j >= n || l >= n) continue;
+        if (!PF) {
+            Gw[(long long)l * n + j] = sT[ty + 8 * q][tx];
+        } else {
+            double v;
+            if (j < l) v = sT[ty + 8 * q][tx];
+            else if (j == l) v = 0.0;
+            else v = -sT[tx][ty + 8 * q];
+            Gw[(long long)l * n + j] = v;
+        }
+    }
+    if (PF && tJ != tL) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int l = l0 + tx, j = j0 + ty + 8 * q;
+            if (j < n && l < n) Gw[(long long)j * n + l] = -sT[tx][ty + 8 * q];
+        }
+    }
+    __syncthreads();
+}
+
+template <bool PF>
+__global__ void __launch_bounds__(256) k_flush_df(DevLayout L, DevState<double> S, const uint8_t* force) {
+    __shared__ DfFlushSmem sm;
+    TileIter ti;
+    for (int w = 0; w < L.W; ++w) {
+        const int tau = S.tau[w];
+        const bool go = force ? (force[w] && tau > 0) : (tau >= L.K);
+        if (!go) continue;
+        const int nt = (L.nw(w) + 31) / 32;
+        const int ntl = TileIter::tiles(nt, PF);
+        for (long long t = ti.first(ntl); t < ntl; t += gridDim.x) {
+            int tJ, tL;
+            TileIter::coords(t, nt, PF, tJ, tL);
+            flush_df_tile<PF>(L, S, w, tau, tJ, tL, sm);
+        }
+    }
+}
+
+#endif
 
 // After the accept pass: log|value| += log|r|, sign *= r/|r|, tau += 1 (delayed)
 template <typename T>
@@ -504,20 +683,36 @@ __global__ void k_commit(DevLayout L, DevState<T> S, const uint8_t* mask, bool d
 // tiles with J <= L are computed and the mirror is written as the exact
 // negative transpose, so A_0^{-1} stays exactly skew.
 // ---------------------------------------------------------------------------
+// The (walker, tile) work of a flush, enumerated without atomics: every CTA
+// scans the walkers, keeps a running tile offset over those that flush now
+// and takes the tiles whose global index is congruent to its block index.
+// Pfaffian tiles cover J <= L only.
+struct TileIter {
+    long long offset = 0;
+    __device__ static int tiles(int nt, bool pf) { return pf ? nt * (nt + 1) / 2 : nt * nt; }
+    __device__ static void coords(long long ti, int nt, bool pf, int& tJ, int& tL) {
+        if (pf) {
+            int r = 0, rem = (int)ti;
+            while (rem >= nt - r) { rem -= nt - r; ++r; }
+            tJ = r;
+            tL = r + rem;
+        } else {
+            tJ = (int)(ti % nt);
+            tL = (int)(ti / nt);
+        }
+    }
+    __device__ long long first(int ntiles) {
+        long long f = ((long long)blockIdx.x - offset) % gridDim.x;
+        if (f < 0) f += gridDim.x;
+        offset += ntiles;
+        return f;
+    }
+};
+
 template <typename T, bool PF>
-__global__ void __launch_bounds__(256) k_flush_native(DevLayout L, DevState<T> S, const uint8_t* force) {
-    __shared__ T sP[32][65];
-    __shared__ T sQ[32][65];
-    __shared__ T sT[32][33];
-    const int w = blockIdx.z;
+__device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int w, int tau, int tJ, int tL,
+                                  T (*sP)[65], T (*sQ)[65], T (*sT)[33]) {
     const int n = L.nw(w), kk = L.kv(w);
-    const int tau = S.tau[w];
-    const bool go = force ? (force[w] && tau > 0) : (tau >= L.K);
-    if (!go) return;
-    const int nt = (n + 31) / 32;
-    const int tJ = blockIdx.x, tL = blockIdx.y;
-    if (tJ >= nt || tL >= nt) return;
-    if (PF && tJ > tL) return;
     const int cu = tau * kk, Kc = L.Kc;
     const long long vo = L.vo(w);
     T* Gw = S.G + L.mo(w);
@@ -582,6 +777,27 @@ __global__ void __launch_bounds__(256) k_flush_native(DevLayout L, DevState<T> S
             }
         }
     }
+    __syncthreads();
+}
+
+template <typename T, bool PF>
+__global__ void __launch_bounds__(256) k_flush_native(DevLayout L, DevState<T> S, const uint8_t* force) {
+    __shared__ T sP[32][65];
+    __shared__ T sQ[32][65];
+    __shared__ T sT[32][33];
+    TileIter ti;
+    for (int w = 0; w < L.W; ++w) {
+        const int tau = S.tau[w];
+        const bool go = force ? (force[w] && tau > 0) : (tau >= L.K);
+        if (!go) continue;
+        const int nt = (L.nw(w) + 31) / 32;
+        const int ntl = TileIter::tiles(nt, PF);
+        for (long long t = ti.first(ntl); t < ntl; t += gridDim.x) {
+            int tJ, tL;
+            TileIter::coords(t, nt, PF, tJ, tL);
+            flush_native_tile<T, PF>(L, S, w, tau, tJ, tL, sP, sQ, sT);
+        }
+    }
 }
 
 template <typename T>
@@ -591,6 +807,30 @@ __global__ void k_flush_finish(DevLayout L, DevState<T> S, const uint8_t* force)
     const int tau = S.tau[w];
     const bool go = force ? (force[w] && tau > 0) : (tau >= L.K);
     if (go) S.tau[w] = 0;
+}
+
+// forced partial flush with the tensor cores: the MMA runs over all Kc slot
+// columns, so the unfilled ones (>= tau * k) must hold zeros in the P split
+template <typename T>
+__global__ void k_zero_split_tail(DevLayout L, DevState<T> S, const uint8_t* force) {
+    const int w = blockIdx.y;
+    if (!force || !force[w]) return;
+    const int cu = S.tau[w] * L.kv(w);
+    if (cu <= 0 || cu >= L.Kc) return;
+    const int n = L.nw(w);
+    const long long vo = L.vo(w);
+    const int width = L.Kc - cu;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * width;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long off = (vo + e / width) * L.Kc32 + cu + e % width;
+        S.P32h[off] = 0.f;
+        S.P32l[off] = 0.f;
+    }
+}
+
+template <typename T>
+void launch_zero_split_tail(const DevLayout& L, const DevState<T>& S, const uint8_t* force, cudaStream_t st) {
+    k_zero_split_tail<T><<<dim3(16, L.W), 256, 0, st>>>(L, S, force);
 }
 
 template <typename T>
@@ -739,10 +979,16 @@ template <typename T, bool DELAYED>
 static void accept_npl(int npl, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
                        const uint8_t* mask, const int* items, int nitems, size_t dyn, cudaStream_t st) {
     const int4* it = reinterpret_cast<const int4*>(items);
-#define LRU_ACC(N)                                                                                      \
-    case N:                                                                                             \
-        cudaFuncSetAttribute(k_accept<T, DELAYED, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn); \
-        k_accept<T, DELAYED, N><<<nitems, PT, dyn, st>>>(L, S, V, mask, it);                             \
+    const bool rank1 = L.kk == 1 && L.kvec == nullptr;
+#define LRU_ACC(N)                                                                                          \
+    case N:                                                                                                 \
+        if (rank1) {                                                                                        \
+            cudaFuncSetAttribute(k_accept<T, DELAYED, N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn); \
+            k_accept<T, DELAYED, N, 1><<<nitems, PT, dyn, st>>>(L, S, V, mask, it);                          \
+        } else {                                                                                            \
+            cudaFuncSetAttribute(k_accept<T, DELAYED, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn); \
+            k_accept<T, DELAYED, N, 0><<<nitems, PT, dyn, st>>>(L, S, V, mask, it);                          \
+        }                                                                                                   \
         break;
     switch (npl) {
         LRU_ACC(1) LRU_ACC(2) LRU_ACC(4) LRU_ACC(8) LRU_ACC(16) LRU_ACC(32) LRU_ACC(64)
@@ -752,17 +998,29 @@ static void accept_npl(int npl, const DevLayout& L, const DevState<T>& S, const 
 }
 
 template <typename T>
-void launch_accept(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
+void launch_accept(bool pf, bool delayed, bool df, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
                    const uint8_t* mask, const int* items, int nitems, cudaStream_t st) {
-    (void)pf;
     const int nmax = L.n_max;
     int npl = 1;
     while (32 * npl < nmax) npl *= 2;
     size_t dyn = (size_t)2 * L.kk * nmax * sizeof(T);
     if (dyn > 160 * 1024) dyn = 0;   // items carry use_smem = 0 in that case (set by the API)
     if (nitems > 0) {
-        if (delayed) accept_npl<T, true>(npl, L, S, V, mask, items, nitems, dyn, st);
-        else accept_npl<T, false>(npl, L, S, V, mask, items, nitems, dyn, st);
+        bool done = false;
+        if constexpr (std::is_same<T, double>::value) {
+            if (df && delayed && !pf && L.kk == 1 && !(V.mask & 1u) && L.n_max <= 2048) {
+                const int4* it = reinterpret_cast<const int4*>(items);
+#define LRU_ACC_DF(N) \
+    case N: k_accept_delayed_df<N><<<nitems, PT, 0, st>>>(L, S, V, mask, it); break;
+                switch (npl) { LRU_ACC_DF(1) LRU_ACC_DF(2) LRU_ACC_DF(4) LRU_ACC_DF(8) LRU_ACC_DF(16) LRU_ACC_DF(32) LRU_ACC_DF(64) default: break; }
+#undef LRU_ACC_DF
+                done = true;
+            }
+        }
+        if (!done) {
+            if (delayed) accept_npl<T, true>(npl, L, S, V, mask, items, nitems, dyn, st);
+            else accept_npl<T, false>(npl, L, S, V, mask, items, nitems, dyn, st);
+        }
     }
     k_commit<T><<<(L.W + 255) / 256, 256, 0, st>>>(L, S, mask, delayed);
 }
@@ -770,11 +1028,25 @@ void launch_accept(bool pf, bool delayed, const DevLayout& L, const DevState<T>&
 template <typename T>
 void launch_flush_native(bool pf, const DevLayout& L, const DevState<T>& S, const uint8_t* force_mask,
                          int nmax, cudaStream_t st) {
-    const int nt = (nmax + 31) / 32;
-    dim3 grid(nt, nt, L.W);
-    if (pf) k_flush_native<T, true><<<grid, 256, 0, st>>>(L, S, force_mask);
-    else k_flush_native<T, false><<<grid, 256, 0, st>>>(L, S, force_mask);
+    (void)nmax;
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (pf) k_flush_native<T, true><<<4 * nsm, 256, 0, st>>>(L, S, force_mask);
+    else k_flush_native<T, false><<<4 * nsm, 256, 0, st>>>(L, S, force_mask);
 }
+
+#if !defined(LRU_INST_DTYPE) || defined(LRU_INST_PRIMARY)
+void launch_flush_df(bool pf, const DevLayout& L, const DevState<double>& S, const uint8_t* force_mask,
+                     cudaStream_t st) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (pf) k_flush_df<true><<<4 * nsm, 256, 0, st>>>(L, S, force_mask);
+    else k_flush_df<false><<<4 * nsm, 256, 0, st>>>(L, S, force_mask);
+}
+
+#endif
 
 template <typename T>
 void launch_flush_finish(const DevLayout& L, const DevState<T>& S, const uint8_t* force_mask, cudaStream_t st) {
@@ -819,12 +1091,13 @@ void launch_commit_moves(int W, int n, int* occ, const int* slot, const int* new
 #define LRU_INST(T)                                                                                          \
     template void launch_propose<T>(bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&,    \
                                     const DevOperand&, const T*, T*, int*, cudaStream_t);                   \
-    template void launch_accept<T>(bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&,     \
+    template void launch_accept<T>(bool, bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&, \
                                    const uint8_t*, const int*, int, cudaStream_t);                          \
     template void launch_flush_native<T>(bool, const DevLayout&, const DevState<T>&, const uint8_t*, int,   \
                                          cudaStream_t);                                                     \
     template void launch_flush_finish<T>(const DevLayout&, const DevState<T>&, const uint8_t*, cudaStream_t); \
     template void launch_set_delay_zero<T>(const DevLayout&, const DevState<T>&, cudaStream_t);             \
+    template void launch_zero_split_tail<T>(const DevLayout&, const DevState<T>&, const uint8_t*, cudaStream_t); \
     template void launch_get_inverse<T>(bool, bool, const DevLayout&, const DevState<T>&, T*, cudaStream_t); \
     template void launch_form_row_moves<T>(const DevLayout&, const T*, int, const int*, const int*,         \
                                            const int*, T*, int*, cudaStream_t);                             \

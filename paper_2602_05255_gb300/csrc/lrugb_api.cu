@@ -38,7 +38,8 @@ struct lru_ctx {
     lru_config cfg;
     int dtype = 0;
     bool pf = false, delayed = false;
-    int W = 0, kk = 0, K = 0, Kc = 0, flush = 0;
+    int W = 0, kk = 0, K = 0, Kc = 0, Kc32 = 0, flush = 0;
+    bool df = false;
     int device = 0;
     cudaStream_t stream = nullptr;
     int n_uni = 0, n_max = 0;
@@ -88,6 +89,8 @@ struct lru_ctx {
         L.kvec = d_kv;
         L.Kc = Kc;
         L.K = K;
+        L.Kc32 = Kc32;
+        L.rows = sum_n;
         return L;
     }
     template <typename T>
@@ -192,10 +195,13 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     const int kk = cfg->kind == LRU_PF ? 2 * cfg->k : cfg->k;
     if (kk > MAXKK) return LRU_ERR_ARG;
     if (cfg->delay < 0) return LRU_ERR_ARG;
-    if (cfg->flush < LRU_FLUSH_NATIVE || cfg->flush > LRU_FLUSH_BF16X3) return LRU_ERR_ARG;
+    if (cfg->flush < LRU_FLUSH_NATIVE || cfg->flush > LRU_FLUSH_DF) return LRU_ERR_ARG;
+    if (cfg->arith != LRU_ARITH_NATIVE && cfg->arith != LRU_ARITH_DF) return LRU_ERR_ARG;
     const bool delayed = cfg->delay >= 2;
     if (delayed && cfg->delay * kk > MAXKC) return LRU_ERR_ARG;
     if (cfg->flush != LRU_FLUSH_NATIVE && !(delayed && cfg->dtype == LRU_F64)) return LRU_ERR_UNSUPPORTED;
+    if (cfg->flush == LRU_FLUSH_BF16 || cfg->flush == LRU_FLUSH_BF16X3) return LRU_ERR_UNSUPPORTED;
+    if (cfg->flush == LRU_FLUSH_DF && !(delayed && cfg->dtype == LRU_F64)) return LRU_ERR_UNSUPPORTED;
 
     lru_ctx* h = new (std::nothrow) lru_ctx();
     if (!h) return LRU_ERR_NOMEM;
@@ -209,8 +215,10 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     h->kk = kk;
     h->K = delayed ? cfg->delay : 0;
     h->Kc = delayed ? cfg->delay * kk : 0;
+    h->Kc32 = (h->Kc + 31) / 32 * 32;
     h->flush = cfg->flush;
     h->device = cfg->device;
+    h->df = cfg->arith == LRU_ARITH_DF && cfg->dtype == LRU_F64;
 
     // geometry
     h->n_h.resize(h->W);
@@ -266,13 +274,13 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     h->nitems = (int)items.size() / 4;
 
     // one allocation: persistent state first, then scratch and metadata
-    const bool tc = delayed && cfg->flush != LRU_FLUSH_NATIVE;
+    const bool tc = delayed && cfg->flush != LRU_FLUSH_NATIVE && cfg->flush != LRU_FLUSH_DF;
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b); return o; };
     const size_t oG = take((size_t)h->sum_n2 * sz);
     const size_t oP = delayed ? take((size_t)h->sum_n * h->Kc * sz) : 0;
     const size_t oQ = delayed ? take((size_t)h->sum_n * h->Kc * sz) : 0;
-    const size_t o32 = tc ? take((size_t)4 * h->sum_n * h->Kc * sizeof(float)) : 0;
+    const size_t o32 = tc ? take((size_t)4 * h->sum_n * h->Kc32 * sizeof(float)) : 0;
     const size_t oTau = take((size_t)h->W * sizeof(int));
     const size_t oLog = take((size_t)h->W * sizeof(double));
     const size_t oSgn = take((size_t)h->W * sz);
@@ -299,7 +307,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     h->G = b + oG;
     if (delayed) { h->P = b + oP; h->Q = b + oQ; }
     if (tc) {
-        const size_t e = (size_t)h->sum_n * h->Kc;
+        const size_t e = (size_t)h->sum_n * h->Kc32;
         h->P32h = (float*)(b + o32);
         h->P32l = h->P32h + e;
         h->Q32h = h->P32l + e;
@@ -463,7 +471,10 @@ static lru_status do_flush(lru_handle h, const uint8_t* force) {
     DevLayout L = h->layout();
     prof_begin(h, LRU_PROF_FLUSH);
     h->launches += 2;
-    if (h->flush != LRU_FLUSH_NATIVE) {
+    if (h->flush == LRU_FLUSH_DF) {
+        launch_flush_df(h->pf, L, h->state<double>(), force, h->stream);
+    } else if (h->flush != LRU_FLUSH_NATIVE) {
+        if (force) LRU_DISPATCH(h, { launch_zero_split_tail<T>(L, h->state<T>(), force, h->stream); });
         if (!launch_flush_tc(h->flush, h->pf, L, (double*)h->G, h->P32h, h->P32l, h->Q32h, h->Q32l, h->tau,
                              force, h->err, h->stream))
             return LRU_ERR_UNSUPPORTED;
@@ -485,7 +496,7 @@ lru_status lru_accept(lru_handle h, const uint8_t* mask) {
     h->launches += (nitems > 0 ? 1 : 0) + 1;
     prof_begin(h, LRU_PROF_ACCEPT);
     LRU_DISPATCH(h, {
-        launch_accept<T>(h->pf, h->delayed, L, h->state<T>(), h->lastV, mask, h->d_items, nitems, h->stream);
+        launch_accept<T>(h->pf, h->delayed, h->df, L, h->state<T>(), h->lastV, mask, h->d_items, nitems, h->stream);
     });
     prof_end(h, LRU_PROF_ACCEPT);
     lru_status s = cuda_check();

@@ -29,7 +29,8 @@ _lib = C.CDLL(LIB_PATH)
 
 F64, C128, F32, C64 = 0, 1, 2, 3
 DET, PF = 0, 1
-FLUSH_NATIVE, FLUSH_TF32X3, FLUSH_TF32, FLUSH_BF16, FLUSH_BF16X3 = 0, 1, 2, 3, 4
+FLUSH_NATIVE, FLUSH_TF32X3, FLUSH_TF32, FLUSH_BF16, FLUSH_BF16X3, FLUSH_DF = 0, 1, 2, 3, 4, 5
+ARITH_NATIVE, ARITH_DF = 0, 1
 WALKER_OK, WALKER_SINGULAR, WALKER_NONFINITE, WALKER_BAD_INDEX = 0, 1, 2, 3
 
 _DTYPES = {torch.float64: F64, torch.complex128: C128, torch.float32: F32, torch.complex64: C64}
@@ -50,7 +51,7 @@ class _Config(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("walkers", C.c_int64), ("n", C.c_int32),
                 ("n_per_walker", C.POINTER(C.c_int32)), ("k", C.c_int32),
                 ("k_per_walker", C.POINTER(C.c_int32)), ("delay", C.c_int32), ("flush", C.c_int32),
-                ("device", C.c_int32)]
+                ("device", C.c_int32), ("arith", C.c_int32)]
 
 
 class _Operand(C.Structure):
@@ -160,7 +161,8 @@ class LowRankState:
     delayed flush (FLUSH_*)."""
 
     def __init__(self, kind: str, walkers: int, n, k: int = 1, dtype=torch.float64, delay: int = 0,
-                 flush: int = FLUSH_NATIVE, k_per_walker=None, device: Optional[int] = None):
+                 flush: int = FLUSH_NATIVE, k_per_walker=None, device: Optional[int] = None,
+                 arith: int = ARITH_NATIVE):
         self.kind = {"det": DET, "pf": PF}[kind]
         self.dtype = dtype
         self.W = int(walkers)
@@ -190,6 +192,7 @@ class LowRankState:
         cfg.delay = self.delay
         cfg.flush = int(flush)
         cfg.device = dev
+        cfg.arith = int(arith)
         h = _H()
         _check(_lib.lru_create(C.byref(cfg), C.byref(h)), "lru_create")
         self._h = h

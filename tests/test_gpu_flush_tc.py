@@ -1,0 +1,173 @@
+"""GPU parity of the delayed flush in its precisions (Sec. 2.3 Eq. delayed_Ainv,
+Sec. 3.3 Eq. pf_delayed_Ainv) and of the double-float GEMV.
+
+- Tensor-core flush (tcgen05, TF32 splits, FP32 accumulation): checked on a
+  well-conditioned chain, where the error is the flush's own.  Bounds from the
+  arithmetic: TF32x3 (3-term split, ~2^-21 per product) 2e-6 relative on ratios
+  and A^{-1}; TF32 (11-bit operands) 2e-3.  On ill-conditioned Slater chains
+  the condition number amplifies any FP32-class flush error (even an exact
+  FP32 GEMM); bench.py reports that drift instead of asserting it.
+- Double-float flush and GEMV (FP32 pipe, ~1e-14): the FP64 bar (relative
+  1e-10, condition-aware) on realistic Slater and pairing chains.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import (O, check_ratios, det_workload, fro_rel, lrugb, pf_workload, rel, replay_det_oracle,
+                        run_det_chain_gpu, tdev, torch)
+
+pytestmark = pytest.mark.gpu
+
+BOUND = {1: 2e-6, 2: 2e-3}
+
+
+def well_conditioned_chain(L, W, n, K, steps, flush, arith, seed):
+    g = np.random.Generator(np.random.PCG64(seed))
+    A = 3.0 * np.eye(n) + g.standard_normal((W, n, n)) / np.sqrt(n)
+    st = L.LowRankState("det", W, n, k=1, dtype=torch.float64, delay=K, flush=flush, arith=arith)
+    st.init(tdev(A))
+    cars = [O.init_det_carrier(A[w], K) for w in range(W)]
+    worst = 0.0
+    for s in range(steps):
+        rows = g.integers(0, n, (W, 1)).astype(np.int32)
+        Vd = g.standard_normal((W, 1, n)) * 0.3 / np.sqrt(n)
+        r, status = st.propose_det(L.Operand(idx=tdev(rows), onehot_mask=1), L.Operand(dense=tdev(Vd)))
+        st.accept()
+        r = r.cpu().numpy()
+        assert (status.cpu().numpy() == 0).all()
+        for w in range(W):
+            ref = O.det_lru_delayed(cars[w], O.onehot_matrix(n, rows[w]), Vd[w])
+            worst = max(worst, rel(r[w], ref))
+    inv = st.inverse().cpu().numpy()
+    inv_err = max(fro_rel(inv[w], O.carrier_inverse(cars[w])) for w in range(W))
+    return st, worst, inv_err
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("n", [200, 256])
+def test_tc_flush_precision(mode, n):
+    # K = 16: 40 steps = two full flushes + 8 pending; n = 200 leaves partial
+    # 128-row tiles that cross into the next walker's rows
+    L = lrugb()
+    st, worst, inv_err = well_conditioned_chain(L, 5, n, 16, 40, mode, L.ARITH_DF, 500 + n)
+    assert worst <= BOUND[mode], worst
+    assert inv_err <= BOUND[mode], inv_err
+    st.check_device_error()
+
+
+@pytest.mark.parametrize("n", [200, 256])
+def test_df_flush_precision(n):
+    L = lrugb()
+    st, worst, inv_err = well_conditioned_chain(L, 5, n, 16, 40, L.FLUSH_DF, L.ARITH_DF, 600 + n)
+    assert worst <= 1e-12 and inv_err <= 1e-12, (worst, inv_err)
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+@pytest.mark.parametrize("flush", [0, 5])
+def test_det_delayed_fp64_class_on_slater_chain(arith, flush):
+    # realistic Slater chain (Phi N(0, 1/n), ill-conditioned): native FP64 or
+    # double-float GEMV, FP64 or double-float flush, all at the FP64 bar
+    L = lrugb()
+    W, n, K, steps = 5, 200, 16, 40
+    Phi, occ0, slot, new = det_workload(700 + n, W, n, 2 * n, steps)
+    st, ratios, status, _ = run_det_chain_gpu(L, Phi, occ0, slot, new, delay=K, flush=flush, arith=arith)
+    assert (status == 0).all()
+    inv = st.inverse().cpu().numpy()
+    # double-float arithmetic has unit roundoff 2^-47 = 64 x FP64's
+    scale = 64.0 if (arith == 1 or flush == 5) else 1.0
+    for w in range(W):
+        rs, inv_ref, _, ex = replay_det_oracle(Phi, occ0, slot, new, w, delay=K)
+        check_ratios(ratios[:, w], rs, ex, what=w, eps_scale=scale)
+        assert fro_rel(inv[w], inv_ref) <= 1e-10 * scale
+
+
+def test_det_tc_matches_native_before_first_flush():
+    # until the first flush the two flush modes run identical FP64 arithmetic
+    L = lrugb()
+    W, n, m, steps, K = 3, 128, 256, 15, 16
+    Phi, occ0, slot, new = det_workload(401, W, n, m, steps)
+    _, r_tc, _, _ = run_det_chain_gpu(L, Phi, occ0, slot, new, delay=K, flush=1)
+    _, r_nat, _, _ = run_det_chain_gpu(L, Phi, occ0, slot, new, delay=K, flush=0)
+    assert np.array_equal(r_tc, r_nat)
+
+
+def test_det_rank2_two_k_chunks():
+    # k = 2 two-row moves, K = 32: 64 slot columns = two 32-wide K chunks of the MMA
+    L = lrugb()
+    W, n, K, steps = 3, 300, 32, 70
+    g = np.random.Generator(np.random.PCG64(411))
+    A = g.standard_normal((W, n, n)) / np.sqrt(n) + 2.0 * np.eye(n)
+    st = L.LowRankState("det", W, n, k=2, dtype=torch.float64, delay=K, flush=1)
+    st.init(tdev(A))
+    cars = [O.init_det_carrier(A[w], K) for w in range(W)]
+    worst = 0.0
+    for s in range(steps):
+        rows = np.stack([g.choice(n, 2, replace=False) for _ in range(W)]).astype(np.int32)
+        Vd = g.standard_normal((W, 2, n)) * 0.05
+        r, status = st.propose_det(L.Operand(idx=tdev(rows), onehot_mask=0b11), L.Operand(dense=tdev(Vd)))
+        st.accept()
+        r = r.cpu().numpy()
+        for w in range(W):
+            U = O.onehot_matrix(n, rows[w])
+            ref = O.det_lru_delayed(cars[w], U, Vd[w])
+            worst = max(worst, rel(r[w], ref))
+    assert worst <= 2e-6, worst
+    inv = st.inverse().cpu().numpy()
+    for w in range(W):
+        assert fro_rel(inv[w], O.carrier_inverse(cars[w])) <= 2e-6
+    assert (st.tau().cpu().numpy() == steps % K).all()
+
+
+@pytest.mark.parametrize("flush", [1, 5])
+def test_pf_delayed_flush_exactly_skew(flush):
+    L = lrugb()
+    W, n, m, steps, K = 4, 136, 300, 16, 8
+    F, pos0, slot, new = pf_workload(421, W, n, m, steps)
+    st = L.LowRankState("pf", W, n, k=1, dtype=torch.float64, delay=K, flush=flush)
+    F_d, pos_d = tdev(F), tdev(pos0)
+    st.init(st.gather_pairs(F_d, pos_d))
+    ratios = []
+    for s in range(steps):
+        B, idx = st.form_pf_moves(F_d, pos_d, tdev(slot[s]), tdev(new[s]))
+        r, _ = st.propose_pf(L.Operand(dense=B, idx=idx, onehot_mask=0b10))
+        st.accept()
+        st.commit_moves(pos_d, tdev(slot[s]), tdev(new[s]))
+        ratios.append(r.cpu().numpy())
+    ratios = np.array(ratios)
+    assert (st.tau().cpu().numpy() == 0).all()
+    inv = st.inverse().cpu().numpy()      # = A_0^{-1} right after the second flush
+    # double-float flush: the FP64 bar with its 64x unit roundoff; the TF32x3
+    # flush on this ill-conditioned pairing chain: an FP32-class bound
+    tol, scale = (1e-10, 64.0) if flush == 5 else (1e-2, 1.0)
+    for w in range(W):
+        assert np.array_equal(inv[w], -inv[w].T)
+        pos = pos0[w].copy()
+        car = O.init_pf_carrier(O.pairing_matrix(F, pos), K)
+        chain, exact = [], []
+        for s in range(steps):
+            B, C = O.pf_row_col_move(F, pos, slot[s, w], new[s, w])
+            exact.append(O.pf_ratio_direct(O.pairing_matrix(F, pos), B, C))
+            chain.append(O.pf_lru_delayed(car, B, C))
+            pos[slot[s, w]] = new[s, w]
+        check_ratios(ratios[:, w], chain, exact, base=tol, what=w, eps_scale=scale)
+        assert fro_rel(inv[w], O.inv(O.pairing_matrix(F, pos))) <= tol * scale
+
+
+@pytest.mark.parametrize("flush", [1, 5])
+def test_forced_partial_flush(flush):
+    # lru_flush_delayed folds tau < K slots; stale columns of earlier windows must not leak in
+    L = lrugb()
+    W, n, K, steps = 4, 160, 8, 23        # 2 full windows, then 7 pending
+    st, _, _ = well_conditioned_chain(L, W, n, K, steps, flush, L.ARITH_DF, 431)
+    before = st.inverse().cpu().numpy()
+    mask = np.array([1, 0, 1, 1], np.uint8)
+    st.flush(tdev(mask))
+    tau = st.tau().cpu().numpy()
+    after = st.inverse().cpu().numpy()
+    tol = 1e-12 if flush == 5 else 2e-6
+    for w in range(W):
+        assert fro_rel(after[w], before[w]) <= tol
+        assert tau[w] == (0 if mask[w] else steps % K)
+        if not mask[w]:
+            assert np.array_equal(after[w], before[w])
+    st.check_device_error()

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from gpu_common import O, RTOL_F64, fro_rel, lrugb, pf_workload, rel, tdev, torch
+from gpu_common import O, RTOL_F64, check_ratios, fro_rel, lrugb, pf_workload, rel, tdev, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -45,14 +45,17 @@ def test_row_col_chain_matches_oracle(cplx, delay):
             car = O.init_pf_carrier(A, delay)
         else:
             Ainv = O.skew_part(O.inv(A))
+        chain, exact = [], []
         for s in range(steps):
             B, C = O.pf_row_col_move(F, pos, slot[s, w], new[s, w])
+            exact.append(O.pf_ratio_direct(O.pairing_matrix(F, pos), B, C))
             if delay:
                 r = O.pf_lru_delayed(car, B, C)
             else:
                 r, Ainv = O.pf_lru(Ainv, B, C, return_update=True)
-            assert rel(ratios[s, w], r) <= RTOL_F64, (s, w, ratios[s, w], r)
+            chain.append(r)
             pos[slot[s, w]] = new[s, w]
+        check_ratios(ratios[:, w], chain, exact, what=w)
         assert np.array_equal(pos, pos_end[w])
         ref = O.carrier_inverse(car) if delay else Ainv
         assert fro_rel(inv_gpu[w], ref) <= RTOL_F64
