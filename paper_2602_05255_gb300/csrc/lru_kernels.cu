@@ -58,6 +58,32 @@ __device__ void block_reduce_vec(T (&v)[NV], T* red, T* out) {
     __syncthreads();
 }
 
+// The (walker, tile) work of a flush, enumerated without atomics: every CTA
+// scans the walkers, keeps a running tile offset over those that flush now
+// and takes the tiles whose global index is congruent to its block index.
+// Pfaffian tiles cover J <= L only.
+struct TileIter {
+    long long offset = 0;
+    __device__ static int tiles(int nt, bool pf) { return pf ? nt * (nt + 1) / 2 : nt * nt; }
+    __device__ static void coords(long long ti, int nt, bool pf, int& tJ, int& tL) {
+        if (pf) {
+            int r = 0, rem = (int)ti;
+            while (rem >= nt - r) { rem -= nt - r; ++r; }
+            tJ = r;
+            tL = r + rem;
+        } else {
+            tJ = (int)(ti % nt);
+            tL = (int)(ti / nt);
+        }
+    }
+    __device__ long long first(int ntiles) {
+        long long f = ((long long)blockIdx.x - offset) % gridDim.x;
+        if (f < 0) f += gridDim.x;
+        offset += ntiles;
+        return f;
+    }
+};
+
 // ---------------------------------------------------------------------------
 // propose: X = A^{-1} U (delayed: A_0^{-1} U -/+ P (Q^T U)), core, small solve
 // det: Sec. 2.1 Eq. det_R, delayed Sec. 2.3 (R_tau, a_tau equations)
@@ -683,32 +709,6 @@ __global__ void k_commit(DevLayout L, DevState<T> S, const uint8_t* mask, bool d
 // tiles with J <= L are computed and the mirror is written as the exact
 // negative transpose, so A_0^{-1} stays exactly skew.
 // ---------------------------------------------------------------------------
-// The (walker, tile) work of a flush, enumerated without atomics: every CTA
-// scans the walkers, keeps a running tile offset over those that flush now
-// and takes the tiles whose global index is congruent to its block index.
-// Pfaffian tiles cover J <= L only.
-struct TileIter {
-    long long offset = 0;
-    __device__ static int tiles(int nt, bool pf) { return pf ? nt * (nt + 1) / 2 : nt * nt; }
-    __device__ static void coords(long long ti, int nt, bool pf, int& tJ, int& tL) {
-        if (pf) {
-            int r = 0, rem = (int)ti;
-            while (rem >= nt - r) { rem -= nt - r; ++r; }
-            tJ = r;
-            tL = r + rem;
-        } else {
-            tJ = (int)(ti % nt);
-            tL = (int)(ti / nt);
-        }
-    }
-    __device__ long long first(int ntiles) {
-        long long f = ((long long)blockIdx.x - offset) % gridDim.x;
-        if (f < 0) f += gridDim.x;
-        offset += ntiles;
-        return f;
-    }
-};
-
 template <typename T, bool PF>
 __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int w, int tau, int tJ, int tL,
                                   T (*sP)[65], T (*sQ)[65], T (*sT)[33]) {
