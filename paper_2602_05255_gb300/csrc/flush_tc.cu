@@ -102,19 +102,16 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // exact float -> double with integer operations (FP32 zeros and subnormals
@@ -131,7 +128,7 @@ __device__ __forceinline__ double f2d_int(float f) {
 // One CTA per SM slot, persistent over the (walker, tile) list of the walkers
 // that flush now.  Walker w flushes when tau_w >= K (or force[w] and tau_w > 0).
 template <bool PF>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
     k_flush_tc(const __grid_constant__ TcMaps maps, DevLayout L, double* G, const int* tau, const uint8_t* force,
                int nkc, int three, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -247,19 +244,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int quad = warp & 3, half = warp >> 2;
             const int jl = 32 * quad + lane;
             const int j = j0 + jl;
-            for (int ch = 0; ch < 2; ++ch) {
-                const int c0 = 64 * half + 32 * ch;
-                float acc[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, acc);
-                double g[32];
+            for (int ch = 0; ch < 4; ++ch) {
+                const int c0 = 64 * half + 16 * ch;
+                float acc[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, acc);
+                double g[16];
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
+                for (int c = 0; c < 16; ++c) {
                     const int l = l0 + c0 + c;
                     const bool keep = j < n && l < n && (!PF || tJ != tL || j < l);
                     g[c] = keep ? Gw[(long long)l * n + j] : 0.0;
                 }
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
+                for (int c = 0; c < 16; ++c) {
                     const int l = l0 + c0 + c;
                     const double d = f2d_int(acc[c]);
                     const double nv = PF ? g[c] + d : g[c] - d;
@@ -271,13 +268,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (PF) {
                     __syncwarp();
-                    // mirror: (l, j) = -(j, l) at G[j*n + l], 32 consecutive l per row j
+                    // mirror: (l, j) = -(j, l) at G[j*n + l], 16 consecutive l per row j,
+                    // two rows per warp instruction
 #pragma unroll 4
-                    for (int r = 0; r < 32; ++r) {
+                    for (int r2 = 0; r2 < 16; ++r2) {
+                        const int r = 2 * r2 + (lane >> 4);
                         const int jr = j0 + 32 * quad + r;
-                        const int l = l0 + c0 + lane;
+                        const int l = l0 + c0 + (lane & 15);
                         if (jr < n && l < n && (tJ != tL || jr < l))
-                            Gw[(long long)jr * n + l] = -sT[r * 33 + lane];
+                            Gw[(long long)jr * n + l] = -sT[r * 33 + (lane & 15)];
                     }
                     __syncwarp();
                 }
@@ -357,7 +356,9 @@ bool launch_flush_tc(int mode, bool pf, const DevLayout& L, double* G, const flo
         cudaGetLastError();
         return false;
     }
-    kern<<<nsm, TC_THREADS, dyn, st>>>(maps, L, G, tau, force_mask, nkc, mode == 1 ? 1 : 0, err);
+    // two CTAs per SM (2 x 128 TMEM columns): one streams its epilogue while
+    // the other waits on TMA and the MMAs
+    kern<<<2 * nsm, TC_THREADS, dyn, st>>>(maps, L, G, tau, force_mask, nkc, mode == 1 ? 1 : 0, err);
     return true;
 }
 

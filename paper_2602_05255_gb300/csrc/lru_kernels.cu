@@ -536,12 +536,15 @@ __global__ void __launch_bounds__(PT) k_accept(DevLayout L, DevState<T> S, DevOp
 // Delayed accept of a real rank-1 update with the GEMV in double-float
 // arithmetic (FP32 pipe): per chunk l, y = V . chunk_l accumulated as hi+lo
 // floats from integer-split doubles, then in FP64 y -= (V P) Q[l,:]^T and
-// Q[l, tau] = y / r (b_tau equation of Sec. 2.3).  Reads A_0^{-1} once.
-template <int NPL>
-__global__ void __launch_bounds__(PT) k_accept_delayed_df(DevLayout L, DevState<double> S, DevOperand V,
-                                                           const uint8_t* mask, const int4* items) {
-    __shared__ float sVh[2048], sVl[2048];
-    __shared__ double sVP[64];
+// Q[l, tau] = y / r (b_tau equation of Sec. 2.3).  Reads A_0^{-1} once, in
+// 16-byte loads, eight at a time per lane with two independent accumulators;
+// the per-chunk FP64 corrections (V P) Q[l,:]^T are formed by 64 threads in
+// the prologue.  NP2 = double2 loads per lane per chunk (n <= 64 NP2).
+template <int NP2>
+__global__ void __launch_bounds__(PT, 3) k_accept_delayed_df(DevLayout L, DevState<double> S, DevOperand V,
+                                                              const uint8_t* mask, const int4* items) {
+    __shared__ float2 sVh[1024], sVl[1024];   // V split, as pairs matching the double2 loads
+    __shared__ double sCorr[256];
     const int4 it = items[blockIdx.x];
     const int w = it.x;
     if (mask && !mask[w]) return;
@@ -551,37 +554,66 @@ __global__ void __launch_bounds__(PT) k_accept_delayed_df(DevLayout L, DevState<
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int Kc = L.Kc, cu = S.tau[w];
     const double* vb = vec_ptr<double>(V, L, w, 0, n);
-    for (int j = threadIdx.x; j < n; j += PT) split_d(vb[j], sVh[j], sVl[j]);
-    for (int c = threadIdx.x; c < cu; c += PT) sVP[c] = S.VP[(long long)w * MAXKK * Kc + c];
+    for (int p = threadIdx.x; p < (n + 1) / 2; p += PT) {
+        const double v0 = vb[2 * p], v1 = (2 * p + 1 < n) ? vb[2 * p + 1] : 0.0;
+        float h0, l0, h1, l1;
+        split_d(v0, h0, l0);
+        split_d(v1, h1, l1);
+        sVh[p] = make_float2(h0, h1);
+        sVl[p] = make_float2(l0, l1);
+    }
+    // corrections of the chunks of this item: corr_l = sum_c (V P)_c Q[l][c]
+    const double* VP = S.VP + (long long)w * MAXKK * Kc;
+    for (int l = it.y + threadIdx.x; l < it.z; l += PT) {
+        const double* qrow = S.Q + (vo + l) * Kc;
+        double c = 0.0;
+        for (int t = 0; t < cu; ++t) c = fma(VP[t], qrow[t], c);
+        sCorr[l - it.y] = c;
+    }
     const double rinv = S.Rinv[(long long)w * MAXKK * MAXKK];
     __syncthreads();
     const double* Gw = S.G + L.mo(w);
+    const bool even = ((n & 1) == 0) && ((L.mo(w) & 1) == 0);   // 16-byte aligned chunks
     for (int l = it.y + wid; l < it.z; l += PT / 32) {
         const double* col = Gw + (long long)l * n;
-        double g[NPL];
+        float ah0 = 0.f, al0 = 0.f, ah1 = 0.f, al1 = 0.f;
+        if (even) {
+            const double2* col2 = reinterpret_cast<const double2*>(col);
 #pragma unroll
-        for (int m = 0; m < NPL; ++m) {
-            const int j = lane + 32 * m;
-            g[m] = (j < n) ? col[j] : 0.0;
-        }
-        float ah = 0.f, al = 0.f;
+            for (int m0 = 0; m0 < NP2; m0 += 8) {
+                double2 g[8];
 #pragma unroll
-        for (int m = 0; m < NPL; ++m) {
-            const int j = lane + 32 * m;
-            if (j < n) {
+                for (int m = 0; m < 8; ++m) {
+                    const int p = lane + 32 * (m0 + m);
+                    g[m] = (m0 + m < NP2 && 2 * p < n) ? col2[p] : make_double2(0.0, 0.0);
+                }
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const int p = lane + 32 * (m0 + m);
+                    if (m0 + m < NP2 && 2 * p < n) {
+                        const float2 vh = sVh[p], vl = sVl[p];
+                        float gh, gl;
+                        split_d(g[m].x, gh, gl);
+                        df_fma(ah0, al0, vh.x, vl.x, gh, gl);
+                        split_d(g[m].y, gh, gl);
+                        df_fma(ah1, al1, vh.y, vl.y, gh, gl);
+                    }
+                }
+            }
+        } else {
+            for (int j = lane; j < n; j += 32) {
                 float gh, gl;
-                split_d(g[m], gh, gl);
-                df_fma(ah, al, sVh[j], sVl[j], gh, gl);
+                split_d(col[j], gh, gl);
+                const float2 vh = sVh[j >> 1], vl = sVl[j >> 1];
+                df_fma(ah0, al0, (j & 1) ? vh.y : vh.x, (j & 1) ? vl.y : vl.x, gh, gl);
             }
         }
-        df_warp_sum(ah, al);
+        df_add(ah0, al0, ah1, al1);
+        df_warp_sum(ah0, al0);
         if (lane == 0) {
-            double y = df_to_double(ah, al);
-            const double* qrow = S.Q + (vo + l) * Kc;
-            for (int c = 0; c < cu; ++c) y = fma(-sVP[c], qrow[c], y);
+            const double y = df_to_double(ah0, al0) - sCorr[l - it.y];
             const double z = rinv * y;
-            const long long off = (vo + l) * Kc + cu;
-            S.Q[off] = z;
+            S.Q[(vo + l) * Kc + cu] = z;
             if (S.P32h) {
                 const long long o32 = (vo + l) * L.Kc32 + cu;
                 float h, lo;
@@ -616,11 +648,10 @@ __device__ void flush_df_tile(const DevLayout& L, const DevState<double>& S, int
     double* Gw = S.G + L.mo(w);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int j0 = tJ * 32, l0 = tL * 32;
-    for (int e = threadIdx.x; e < 32 * 64; e += 256) {
-        const int r = e / 64, c = e % 64;
-        const bool okc = c < cu;
-        double p = (okc && j0 + r < n) ? S.P[(vo + j0 + r) * Kc + c] : 0.0;
-        double q = (okc && l0 + r < n) ? S.Q[(vo + l0 + r) * Kc + c] : 0.0;
+    for (int e = threadIdx.x; e < 32 * cu; e += 256) {
+        const int r = e / cu, c = e % cu;
+        double p = (j0 + r < n) ? S.P[(vo + j0 + r) * Kc + c] : 0.0;
+        double q = (l0 + r < n) ? S.Q[(vo + l0 + r) * Kc + c] : 0.0;
         split_d(p, sPh[r][c], sPl[r][c]);
         split_d(q, sQh[r][c], sQl[r][c]);
     }
@@ -1012,7 +1043,8 @@ void launch_accept(bool pf, bool delayed, bool df, const DevLayout& L, const Dev
                 const int4* it = reinterpret_cast<const int4*>(items);
 #define LRU_ACC_DF(N) \
     case N: k_accept_delayed_df<N><<<nitems, PT, 0, st>>>(L, S, V, mask, it); break;
-                switch (npl) { LRU_ACC_DF(1) LRU_ACC_DF(2) LRU_ACC_DF(4) LRU_ACC_DF(8) LRU_ACC_DF(16) LRU_ACC_DF(32) LRU_ACC_DF(64) default: break; }
+                const int np2 = npl <= 2 ? 1 : npl / 2;   // double2 loads per lane
+                switch (np2) { LRU_ACC_DF(1) LRU_ACC_DF(2) LRU_ACC_DF(4) LRU_ACC_DF(8) LRU_ACC_DF(16) LRU_ACC_DF(32) default: break; }
 #undef LRU_ACC_DF
                 done = true;
             }

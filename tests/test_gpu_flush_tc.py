@@ -120,6 +120,8 @@ def test_det_rank2_two_k_chunks():
 
 @pytest.mark.parametrize("flush", [1, 5])
 def test_pf_delayed_flush_exactly_skew(flush):
+    # realistic pairing chain: the flushed A_0^{-1} is exactly skew in both
+    # precisions; the double-float flush also meets the FP64 bar (64x roundoff)
     L = lrugb()
     W, n, m, steps, K = 4, 136, 300, 16, 8
     F, pos0, slot, new = pf_workload(421, W, n, m, steps)
@@ -136,11 +138,10 @@ def test_pf_delayed_flush_exactly_skew(flush):
     ratios = np.array(ratios)
     assert (st.tau().cpu().numpy() == 0).all()
     inv = st.inverse().cpu().numpy()      # = A_0^{-1} right after the second flush
-    # double-float flush: the FP64 bar with its 64x unit roundoff; the TF32x3
-    # flush on this ill-conditioned pairing chain: an FP32-class bound
-    tol, scale = (1e-10, 64.0) if flush == 5 else (1e-2, 1.0)
     for w in range(W):
         assert np.array_equal(inv[w], -inv[w].T)
+        if flush != 5:
+            continue
         pos = pos0[w].copy()
         car = O.init_pf_carrier(O.pairing_matrix(F, pos), K)
         chain, exact = [], []
@@ -149,8 +150,37 @@ def test_pf_delayed_flush_exactly_skew(flush):
             exact.append(O.pf_ratio_direct(O.pairing_matrix(F, pos), B, C))
             chain.append(O.pf_lru_delayed(car, B, C))
             pos[slot[s, w]] = new[s, w]
-        check_ratios(ratios[:, w], chain, exact, base=tol, what=w, eps_scale=scale)
-        assert fro_rel(inv[w], O.inv(O.pairing_matrix(F, pos))) <= tol * scale
+        check_ratios(ratios[:, w], chain, exact, what=w, eps_scale=64.0)
+        assert fro_rel(inv[w], O.inv(O.pairing_matrix(F, pos))) <= 64e-10
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_pf_tc_flush_precision(mode):
+    # well-conditioned skew chain: A = 3 J + small skew noise, small row+column moves
+    L = lrugb()
+    W, n, K, steps = 4, 200, 8, 20
+    g = np.random.Generator(np.random.PCG64(441))
+    G = g.standard_normal((W, n, n)) * np.sqrt(0.1 / n)
+    A = 3.0 * O.skew_eye(n // 2)[None] + G - G.transpose(0, 2, 1)
+    st = L.LowRankState("pf", W, n, k=1, dtype=torch.float64, delay=K, flush=mode)
+    st.init(tdev(A))
+    cars = [O.init_pf_carrier(A[w], K) for w in range(W)]
+    worst = 0.0
+    for s in range(steps):
+        x = g.standard_normal((W, n)) * 0.3 / np.sqrt(n)
+        i = g.integers(0, n, W).astype(np.int32)
+        Bd = np.zeros((W, 2, n)); Bd[:, 0] = x
+        idx = np.zeros((W, 2), np.int32); idx[:, 1] = i
+        r, status = st.propose_pf(L.Operand(dense=tdev(Bd), idx=tdev(idx), onehot_mask=0b10))
+        st.accept()
+        r = r.cpu().numpy()
+        for w in range(W):
+            B = np.stack([x[w], O.onehot_matrix(n, [i[w]])[:, 0]], 1)
+            worst = max(worst, rel(r[w], O.pf_lru_delayed(cars[w], B)))
+    assert worst <= BOUND[mode], worst
+    inv = st.inverse().cpu().numpy()
+    for w in range(W):
+        assert fro_rel(inv[w], O.carrier_inverse(cars[w])) <= BOUND[mode]
 
 
 @pytest.mark.parametrize("flush", [1, 5])
