@@ -219,6 +219,23 @@ lru_status lru_gather_pairs(lru_handle h, const void* F, int32_t m, const int32_
 /* slogdet of W matrices of size n (row-major), dtype as given. */
 lru_status lru_slogdet_batched(int32_t dtype, int64_t W, int32_t n, const void* A,
                                double* logabs, void* sign, void* stream);
+/* Same as lru_slogdet_batched, but allocates nothing (the paper has no
+ * counterpart; this is a deployment variant).  For callers that cannot let a
+ * library allocate device memory: runtimes that reserve most of the GPU for
+ * their own memory pool, code that must avoid the device-wide synchronisation
+ * of cudaFree, and code recorded once and replayed later.  The Gauss-Jordan
+ * workspace is a fixed 64 MiB array in the library's device memory, which
+ * every GPU that loads the library holds until the process exits.  Limit:
+ * one n x n matrix must fit it (n * n * sizeof(scalar) <= 64 MiB, so every
+ * n <= 2048 of every dtype); other sizes return LRU_ERR_ARG.  The first call on a
+ * device looks up the workspace's address for that device (a runtime query,
+ * no allocation): make that first call before any stream capture.  All calls
+ * share the one workspace, whose contents persist between calls; every matrix
+ * is copied in before use, so nothing needs clearing, but calls whose work
+ * overlaps on the GPU (different streams or host threads without ordering)
+ * race on it and must be serialised by the caller. */
+lru_status lru_slogdet_batched_noalloc(int32_t dtype, int64_t W, int32_t n, const void* A,
+                                       double* logabs, void* sign, void* stream);
 /* slogpf of W skew matrices of even size n (Parlett-Reid with pivoting). */
 lru_status lru_slogpf_batched(int32_t dtype, int64_t W, int32_t n, const void* A,
                               double* logabs, void* sign, void* stream);

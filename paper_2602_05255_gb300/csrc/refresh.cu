@@ -6,6 +6,8 @@
 #include "common.cuh"
 #include "internal.h"
 
+#include <algorithm>
+
 namespace lru {
 
 constexpr int RT = 256;   // threads per matrix
@@ -446,3 +448,83 @@ LRU_INST_R(c128)
 LRU_INST_R(c64)
 
 }  // namespace lru
+
+// ---------------------------------------------------------------------------
+// slogdet without any allocation (lru_slogdet_batched_noalloc)
+//
+// Some callers cannot let a library allocate device memory: runtimes that
+// preallocate most of the GPU for their own pool (so a cudaMalloc can fail),
+// code that must not hit the device-wide synchronisation of cudaFree, and
+// callers that record work for later replay.  This entry point runs the same
+// Gauss-Jordan kernel as lru_slogdet_batched, with its per-CTA matrix
+// workspace taken from the fixed array below instead of cudaMallocAsync.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+#include "../../include/lrugb.h"
+
+namespace lru {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(64) << 20;   // 64 MiB, held by every GPU that loads the library
+
+// The workspace.  Host code may not use this name as a device address: the
+// address comes from cudaGetSymbolAddress, per device, in noalloc_scratch().
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of the workspace on the current device; looked up once per
+// device, with that device current.  Returns nullptr if the lookup failed.
+static void* noalloc_scratch(int dev) {
+    constexpr int MAXDEV = 64;
+    static std::mutex mu;
+    static void* addr[MAXDEV] = {};
+    static bool done[MAXDEV] = {};
+    if (dev < 0 || dev >= MAXDEV) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;   // not cached: the next call tries again
+        }
+        addr[dev] = p;
+        done[dev] = true;
+    }
+    return addr[dev];
+}
+
+}  // namespace lru
+
+extern "C" lru_status lru_slogdet_batched_noalloc(int32_t dtype, int64_t W, int32_t n, const void* A,
+                                                  double* logabs, void* sign, void* stream) {
+    using namespace lru;
+    size_t sz = 0;
+    switch (dtype) {
+        case LRU_F64: sz = 8; break;
+        case LRU_C128: sz = 16; break;
+        case LRU_F32: sz = 4; break;
+        case LRU_C64: sz = 8; break;
+        default: return LRU_ERR_ARG;
+    }
+    if (W < 1 || W > (int64_t)1 << 31 || n < 1 || n > 2048 || !A || !logabs || !sign) return LRU_ERR_ARG;
+    const size_t per = (size_t)n * n * sz;
+    if (per > NOALLOC_SCRATCH_BYTES) return LRU_ERR_ARG;   // one matrix must fit the workspace
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return LRU_ERR_CUDA; }
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        nsm = 148;
+    }
+    void* ws = noalloc_scratch(dev);
+    if (!ws) return LRU_ERR_CUDA;
+    long long slots = (long long)(NOALLOC_SCRATCH_BYTES / per);
+    slots = std::min<long long>(slots, std::min<long long>(W, 2LL * nsm));
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dtype) {
+        case LRU_F64: launch_slogdet<double>((int)W, n, (const double*)A, (double*)ws, (int)slots, logabs, (double*)sign, st); break;
+        case LRU_C128: launch_slogdet<c128>((int)W, n, (const c128*)A, (c128*)ws, (int)slots, logabs, (c128*)sign, st); break;
+        case LRU_F32: launch_slogdet<float>((int)W, n, (const float*)A, (float*)ws, (int)slots, logabs, (float*)sign, st); break;
+        case LRU_C64: launch_slogdet<c64>((int)W, n, (const c64*)A, (c64*)ws, (int)slots, logabs, (c64*)sign, st); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? LRU_OK : LRU_ERR_CUDA;
+}

@@ -89,6 +89,7 @@ _SIGS = {
     "lru_launch_count": [_H, C.POINTER(_i64)],
     "lru_slogdet_batched": [_i32, _i64, _i32, _vp, _vp, _vp, _vp],
     "lru_slogpf_batched": [_i32, _i64, _i32, _vp, _vp, _vp, _vp],
+    "lru_slogdet_batched_noalloc": [_i32, _i64, _i32, _vp, _vp, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -369,6 +370,19 @@ def slogdet_batched(A: torch.Tensor):
     sign = torch.empty(W, dtype=A.dtype, device=A.device)
     _check(_lib.lru_slogdet_batched(_DTYPES[A.dtype], W, n, _ptr(A), _ptr(logabs), _ptr(sign), _stream()),
            "lru_slogdet_batched")
+    return sign, logabs
+
+
+def slogdet_batched_noalloc(A: torch.Tensor, logabs=None, sign=None):
+    """slogdet_batched without any device allocation by the library: the
+    workspace is a fixed 64 MiB array in the library's device memory, shared by
+    all calls (overlapping calls race; the first call on a device should come
+    before any stream capture).  Pass logabs / sign to avoid allocations here too."""
+    W, n = A.shape[0], A.shape[-1]
+    logabs = torch.empty(W, dtype=torch.float64, device=A.device) if logabs is None else logabs
+    sign = torch.empty(W, dtype=A.dtype, device=A.device) if sign is None else sign
+    _check(_lib.lru_slogdet_batched_noalloc(_DTYPES[A.dtype], W, n, _ptr(A), _ptr(logabs), _ptr(sign), _stream()),
+           "lru_slogdet_batched_noalloc")
     return sign, logabs
 
 
