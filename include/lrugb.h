@@ -185,6 +185,34 @@ lru_status lru_load_state(lru_handle h, const void* buf);
 /* Synchronises the stream and reports (then clears) the sticky device error. */
 lru_status lru_check_device_error(lru_handle h);
 
+/* ---- reverse-mode differentiation (adjoint kernels) ----------------------- */
+
+/* log of the pending proposal's ratios into logr (W scalars): log|r| for real
+ * dtypes, the principal complex log for complex ones. */
+lru_status lru_log_ratio(lru_handle h, void* logr);
+/* Vector-Jacobian product of the pending determinant proposal's log ratio
+ * (Sec. 2.1, Eqs. det_R, det_ratio): g (W scalars) = dL/dlog r.  Writes
+ * gU = g (R^{-1} V A^{-1})^T and gV = g (A^{-1} U R^{-1})^T (operand vector
+ * layout, kmax slots; one-hot slots get the dense gradient too) and
+ * gA = -g (A^{-1} U R^{-1} V A^{-1})^T (W matrices, row-major).  Complex
+ * dtypes return g * conj(J) (the convention of PyTorch's autograd).  Any
+ * output may be NULL.  Call after propose and before accept; walkers whose
+ * proposal status is not OK get zeros.  The delayed state recomputes V A^{-1}
+ * from A_0^{-1} and the stored slots instead of storing A^{-1}. */
+lru_status lru_backward_det(lru_handle h, const void* g, void* gU, void* gV, void* gA);
+/* Same for the Pfaffian proposal (App. A.2 Eq. pf_low_rank, App. A.3 Eq.
+ * pf_grad), with A and C entering through their skew parts (M - M^T)/2:
+ * gB = g X M^{-1} (X = A^{-1} B), gA_ij = g (X M^{-1} X^T)_ji / 2, gC = skew
+ * part of -g [C^{-1} (M^{-1} - C) C^{-1}]^T / 2 (W x 2k x 2k). */
+lru_status lru_backward_pf(lru_handle h, const void* g, void* gB, void* gC, void* gA);
+/* d log|det A| / dA = A^{-T} (det) or d log pf A / dA_ij = (A^{-1})_ji / 2 (pf,
+ * App. A.3 Eq. pf_grad divided by pf), times g (W scalars): gA row-major. */
+lru_status lru_backward_logvalue(lru_handle h, const void* g, void* gA);
+/* gPhi[rows[w][i]][:] += gA[w][i][:] for all walkers (rows: W x n int32 into
+ * the m x n matrix gPhi): the gradient of the orbital matrix Phi through
+ * A_w = Phi[rows_w].  Atomic adds; gPhi is accumulated, not cleared. */
+lru_status lru_scatter_rows_add(lru_handle h, const void* gA, const int32_t* rows, int32_t m, void* gPhi);
+
 /* ---- operand formation for QMC moves (Sec. 2.2, 3.2) --------------------- */
 
 /* Determinant row replacement: walker w moves slot i = slot[w] from orbital

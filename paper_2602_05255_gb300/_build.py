@@ -25,6 +25,7 @@ UNITS = [
     ("lru_kernels.cu", "lru_kernels_c64.o", ["-DLRU_INST_DTYPE=c64"]),
     ("refresh.cu", "refresh.o", []),
     ("flush_tc.cu", "flush_tc.o", []),
+    ("adjoint.cu", "adjoint.o", []),
 ]
 
 

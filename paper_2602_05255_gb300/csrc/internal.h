@@ -109,6 +109,18 @@ void launch_slogpf(const DevLayout& L, const T* A, const uint8_t* mask, T* ws, i
 template <typename T>
 void launch_slogdet(int W, int n, const T* A, T* ws, int nws, double* logabs, T* sgn, cudaStream_t st);
 
+// ---- adjoint (adjoint.cu) ----
+template <typename T>
+void launch_backward(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
+                     const T* C, const T* g, T* ws, T* gU, T* gV, T* gA, T* gC, cudaStream_t st);
+template <typename T>
+void launch_backward_logvalue(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const T* g, T* gA,
+                              cudaStream_t st);
+template <typename T>
+void launch_log_ratio(int W, const T* ratio, T* out, cudaStream_t st);
+template <typename T>
+void launch_scatter_rows(const DevLayout& L, const T* gA, const int* rows, int m, T* gPhi, int* err, cudaStream_t st);
+
 // ---- tensor-core flush (flush_tc.cu) ----
 // Returns false when the combination is not built.
 bool launch_flush_tc(int mode, bool pf, const DevLayout& L, double* G, const float* Ph, const float* Pl,

@@ -75,6 +75,9 @@ struct lru_ctx {
     // last proposal
     bool has_prop = false;
     DevOperand lastV{};
+    const void* lastC = nullptr;
+    // adjoint workspace (allocated on first use)
+    void* bws = nullptr;
     int n_sm = 148;
 
     DevLayout layout() const {
@@ -352,6 +355,7 @@ lru_status lru_destroy(lru_handle h) {
     else cudaDeviceSynchronize();
     cudaFree(h->base);
     if (h->ws) cudaFree(h->ws);
+    if (h->bws) cudaFree(h->bws);
     for (auto& v : h->prof_ev)
         for (auto& e : v) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     cudaGetLastError();
@@ -463,6 +467,7 @@ lru_status lru_propose_pf(lru_handle h, const lru_operand* B, const void* C, voi
     lru_status s = cuda_check();
     if (s != LRU_OK) return s;
     h->lastV = dB;
+    h->lastC = C;
     h->has_prop = true;
     return LRU_OK;
 }
@@ -631,6 +636,63 @@ lru_status lru_gather_pairs(lru_handle h, const void* F, int32_t m, const int32_
     DevLayout L = h->layout();
     h->launches += 1;
     LRU_DISPATCH(h, { launch_gather<T>(true, L, (const T*)F, m, pos, (T*)A_out, h->err, h->stream); });
+    return cuda_check();
+}
+
+lru_status lru_log_ratio(lru_handle h, void* logr) {
+    if (!h || !logr) return LRU_ERR_ARG;
+    if (!h->has_prop) return LRU_ERR_STATE;
+    CK(cudaSetDevice(h->device));
+    h->launches += 1;
+    LRU_DISPATCH(h, { launch_log_ratio<T>(h->W, (const T*)h->ratio, (T*)logr, h->stream); });
+    return cuda_check();
+}
+
+static lru_status do_backward(lru_handle h, bool pf, const void* g, void* gU, void* gV, void* gA, void* gC) {
+    if (!h || !g) return LRU_ERR_ARG;
+    if (h->pf != pf) return LRU_ERR_STATE;
+    if (!h->has_prop) return LRU_ERR_STATE;
+    CK(cudaSetDevice(h->device));
+    if (!h->bws) {
+        if (cudaMalloc(&h->bws, (size_t)2 * h->sum_n * h->kk * dtype_size(h->dtype)) != cudaSuccess) {
+            cudaGetLastError();
+            h->bws = nullptr;
+            return LRU_ERR_NOMEM;
+        }
+    }
+    DevLayout L = h->layout();
+    h->launches += 1;
+    LRU_DISPATCH(h, {
+        launch_backward<T>(pf, h->delayed, L, h->state<T>(), h->lastV, (const T*)h->lastC, (const T*)g, (T*)h->bws,
+                           (T*)gU, (T*)gV, (T*)gA, (T*)gC, h->stream);
+    });
+    return cuda_check();
+}
+
+lru_status lru_backward_det(lru_handle h, const void* g, void* gU, void* gV, void* gA) {
+    return do_backward(h, false, g, gU, gV, gA, nullptr);
+}
+
+lru_status lru_backward_pf(lru_handle h, const void* g, void* gB, void* gC, void* gA) {
+    return do_backward(h, true, g, gB, nullptr, gA, gC);
+}
+
+lru_status lru_backward_logvalue(lru_handle h, const void* g, void* gA) {
+    if (!h || !g || !gA) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    DevLayout L = h->layout();
+    h->launches += 1;
+    LRU_DISPATCH(h, { launch_backward_logvalue<T>(h->pf, h->delayed, L, h->state<T>(), (const T*)g, (T*)gA, h->stream); });
+    return cuda_check();
+}
+
+lru_status lru_scatter_rows_add(lru_handle h, const void* gA, const int32_t* rows, int32_t m, void* gPhi) {
+    if (!h || !gA || !rows || !gPhi || m < 1) return LRU_ERR_ARG;
+    if (h->n_uni <= 0) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    DevLayout L = h->layout();
+    h->launches += 1;
+    LRU_DISPATCH(h, { launch_scatter_rows<T>(L, (const T*)gA, rows, m, (T*)gPhi, h->err, h->stream); });
     return cuda_check();
 }
 

@@ -84,6 +84,11 @@ _SIGS = {
     "lru_commit_moves": [_H, _vp, _vp, _vp, _vp],
     "lru_gather_rows": [_H, _vp, _i32, _vp, _vp],
     "lru_gather_pairs": [_H, _vp, _i32, _vp, _vp],
+    "lru_log_ratio": [_H, _vp],
+    "lru_backward_det": [_H, _vp, _vp, _vp, _vp],
+    "lru_backward_pf": [_H, _vp, _vp, _vp, _vp],
+    "lru_backward_logvalue": [_H, _vp, _vp],
+    "lru_scatter_rows_add": [_H, _vp, _vp, _i32, _vp],
     "lru_profile_enable": [_H, _i32],
     "lru_profile_read": [_H, _i32, C.POINTER(C.c_double), C.POINTER(_i64)],
     "lru_launch_count": [_H, C.POINTER(_i64)],
@@ -307,6 +312,51 @@ class LowRankState:
         self._bind()
         _check(_lib.lru_check_device_error(self._h), "lru_check_device_error")
 
+    # ---- reverse mode --------------------------------------------------------
+    def log_ratio(self) -> torch.Tensor:
+        """log of the pending proposal's ratios (real: log|r|, complex: log r)."""
+        self._bind()
+        out = self._vec_out(self.dtype)
+        _check(_lib.lru_log_ratio(self._h, _ptr(out)), "lru_log_ratio")
+        return out
+
+    def _ops_like(self):
+        n = self.n_list[0]
+        return torch.zeros(self.W, self.kmax, n, dtype=self.dtype, device=self.device)
+
+    def backward_det(self, g: torch.Tensor, want_U=True, want_V=True, want_A=True):
+        """(gU, gV, gA): vector-Jacobian product of the pending proposal's log ratio."""
+        self._bind()
+        n = self.n_list[0]
+        gU = self._ops_like() if want_U else None
+        gV = self._ops_like() if want_V else None
+        gA = torch.empty(self.W, n, n, dtype=self.dtype, device=self.device) if want_A else None
+        _check(_lib.lru_backward_det(self._h, _ptr(g.contiguous()), _ptr(gU), _ptr(gV), _ptr(gA)), "lru_backward_det")
+        return gU, gV, gA
+
+    def backward_pf(self, g: torch.Tensor, want_B=True, want_C=True, want_A=True):
+        """(gB, gC, gA) for the pending Pfaffian proposal (skew parts of A and C)."""
+        self._bind()
+        n = self.n_list[0]
+        gB = self._ops_like() if want_B else None
+        gC = torch.empty(self.W, self.kmax, self.kmax, dtype=self.dtype, device=self.device) if want_C else None
+        gA = torch.empty(self.W, n, n, dtype=self.dtype, device=self.device) if want_A else None
+        _check(_lib.lru_backward_pf(self._h, _ptr(g.contiguous()), _ptr(gB), _ptr(gC), _ptr(gA)), "lru_backward_pf")
+        return gB, gC, gA
+
+    def backward_logvalue(self, g: torch.Tensor) -> torch.Tensor:
+        self._bind()
+        n = self.n_list[0]
+        gA = torch.empty(self.W, n, n, dtype=self.dtype, device=self.device)
+        _check(_lib.lru_backward_logvalue(self._h, _ptr(g.contiguous()), _ptr(gA)), "lru_backward_logvalue")
+        return gA
+
+    def scatter_rows_add(self, gA: torch.Tensor, rows: torch.Tensor, gPhi: torch.Tensor):
+        self._bind()
+        _check(_lib.lru_scatter_rows_add(self._h, _ptr(gA), _ptr(rows), gPhi.shape[0], _ptr(gPhi)),
+               "lru_scatter_rows_add")
+        return gPhi
+
     # ---- profiling ---------------------------------------------------------
     PROF_PROPOSE, PROF_ACCEPT, PROF_FLUSH, PROF_REFRESH = 0, 1, 2, 3
 
@@ -395,3 +445,76 @@ def slogpf_batched(A: torch.Tensor):
     _check(_lib.lru_slogpf_batched(_DTYPES[A.dtype], W, n, _ptr(A), _ptr(logabs), _ptr(sign), _stream()),
            "lru_slogpf_batched")
     return sign, logabs
+
+
+# ---------------------------------------------------------------------------
+# torch.autograd.Function wrappers: the forward is a propose through the
+# C-ABI, the backward the adjoint kernel.  Call loss.backward() before
+# accepting the proposal (accept changes the state the adjoint reads).
+# ---------------------------------------------------------------------------
+class _DetLogRatio(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U, V, A, state):
+        state.propose_det(Operand(dense=U.contiguous()), Operand(dense=V.contiguous()))
+        ctx.state = state
+        ctx.want = (ctx.needs_input_grad[0], ctx.needs_input_grad[1], A is not None and ctx.needs_input_grad[2])
+        return state.log_ratio()
+
+    @staticmethod
+    def backward(ctx, g):
+        gU, gV, gA = ctx.state.backward_det(g, *ctx.want)
+        return gU, gV, gA, None
+
+
+def det_log_ratio(state: LowRankState, U: torch.Tensor, V: torch.Tensor, A: Optional[torch.Tensor] = None):
+    """log det(I + V A^{-1} U) per walker (Sec. 2.1), differentiable in U, V
+    ((W, k, n) dense tensors) and A (the matrices whose inverses the state
+    holds).  Real dtypes give log|r|, complex the principal log r."""
+    return _DetLogRatio.apply(U, V, A, state)
+
+
+class _PfLogRatio(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, B, Cm, A, state):
+        state.propose_pf(Operand(dense=B.contiguous()), None if Cm is None else Cm.contiguous())
+        ctx.state = state
+        ctx.want = (ctx.needs_input_grad[0], Cm is not None and ctx.needs_input_grad[1],
+                    A is not None and ctx.needs_input_grad[2])
+        return state.log_ratio()
+
+    @staticmethod
+    def backward(ctx, g):
+        gB, gC, gA = ctx.state.backward_pf(g, *ctx.want)
+        return gB, gC, gA, None
+
+
+def pf_log_ratio(state: LowRankState, B: torch.Tensor, Cm: Optional[torch.Tensor] = None,
+                 A: Optional[torch.Tensor] = None):
+    """log [pf(C^{-1} + B^T A^{-1} B) / pf(C^{-1})] per walker (App. A.2), differentiable
+    in B ((W, 2k, n)), C ((W, 2k, 2k); None = -J) and A, with A and C entering
+    through their skew parts (App. A.3)."""
+    return _PfLogRatio.apply(B, Cm, A, state)
+
+
+class _OrbitalLogRatio(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, Phi, U, V, state, rows):
+        state.propose_det(Operand(dense=U.contiguous()), Operand(dense=V.contiguous()))
+        ctx.state, ctx.rows, ctx.m = state, rows, Phi.shape[0]
+        ctx.save_for_backward(Phi)
+        return state.log_ratio()
+
+    @staticmethod
+    def backward(ctx, g):
+        (Phi,) = ctx.saved_tensors
+        gU, gV, gA = ctx.state.backward_det(g, True, True, True)
+        gPhi = torch.zeros_like(Phi)
+        ctx.state.scatter_rows_add(gA, ctx.rows, gPhi)
+        return gPhi, gU, gV, None, None
+
+
+def orbital_log_ratio(state: LowRankState, Phi: torch.Tensor, rows: torch.Tensor, U: torch.Tensor,
+                      V: torch.Tensor):
+    """log det(I + V A^{-1} U) with A_w = Phi[rows_w] (the state holds A^{-1}),
+    differentiable in the orbital matrix Phi (through A), U and V."""
+    return _OrbitalLogRatio.apply(Phi, U, V, state, rows)
