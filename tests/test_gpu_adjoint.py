@@ -74,8 +74,7 @@ def test_pf_adjoint(dt, delay):
     cplx = dt == "c128"
     g = np.random.Generator(np.random.PCG64(911 + delay))
     W, n, k = 3, 20, 2
-    A = O.skew_part(rand(g, (W, n, n), cplx))
-    A = np.stack([O.skew_part(a) + 2 * O.skew_eye(n // 2) for a in A])
+    A = np.stack([O.skew_part(a) + 2 * O.skew_eye(n // 2) for a in rand(g, (W, n, n), cplx)])
     st = L.LowRankState("pf", W, n, k=k, dtype=tdt, delay=delay)
     st.init(tdev(A, tdt))
     for s in range(4):
