@@ -100,6 +100,8 @@ typedef struct {
     int32_t flush;                /* lru_flush */
     int32_t device;               /* CUDA device ordinal */
     int32_t arith;                /* lru_arith (F64 handles; ignored otherwise) */
+    int32_t tile_chunks;          /* columns of A^{-1} per CTA work item of the accept pass
+                                     (0 = default min(64, max(8, n/4))); autotuned */
 } lru_config;
 
 /* One operand of a proposal: kmax vector slots per walker (see Conventions).
@@ -166,6 +168,21 @@ lru_status lru_propose_pf(lru_handle h, const lru_operand* B, const void* C,
  * and multiplies the sign/phase.  A walker whose delay slots are full is
  * folded into A_0^{-1} at once (the flush of Eq. delayed_Ainv). */
 lru_status lru_accept(lru_handle h, const uint8_t* mask);
+/* One persistent fused step for all walkers, including walkers of uneven n
+ * and k: a single kernel launch of a fixed grid takes the proposals of every
+ * walker (largest first) and then, unless accept == 0, the accept passes, from
+ * a device work queue, with bounded waits between a walker's propose and its
+ * accept pass.  Acceptance: walkers whose proposal status is OK and, when
+ * given, mask[w] != 0 and |ratio|^2 >= u[w] (u: W doubles, Metropolis
+ * uniforms).  acc_out (W uint8, may be NULL) receives the decisions.  Plain
+ * (non-delayed) handles.  The call issues only a memset and one kernel on the
+ * handle's stream (no allocation, no synchronisation), so it can be captured
+ * in a CUDA graph; make one call before capturing so that one-time kernel
+ * set-up happens outside the capture.  ratio/st as in lru_propose_det; U, V
+ * (det) or B (pf, with C or NULL) as in the propose calls. */
+lru_status lru_step_persistent(lru_handle h, const lru_operand* U, const lru_operand* V, const void* C,
+                               int32_t accept, const uint8_t* mask, const double* u, void* ratio, int32_t* st,
+                               uint8_t* acc_out);
 /* Folds the partial delay slots of the masked walkers into A_0^{-1} now. */
 lru_status lru_flush_delayed(lru_handle h, const uint8_t* mask);
 

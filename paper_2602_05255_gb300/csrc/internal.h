@@ -62,6 +62,21 @@ struct DevOperand {
     int slots;       // vector slots per walker in the buffers (kmax)
 };
 
+// Control block of the persistent fused step (see k_step).
+struct StepCtl {
+    int* counter;             // work-queue head, zeroed before each launch
+    int* prop_done;           // W flags, zeroed before each launch
+    int* items_done;          // W counters, zeroed before each launch
+    uint8_t* acc;             // W accept decisions (output)
+    const int* order;         // W walkers in propose order
+    const int4* acc_items;    // accept items (walker, l0, l1, use_smem), largest walkers first
+    const int* nacc_w;        // accept items per walker
+    int nacc;
+    int do_accept;            // 0: propose only
+    const uint8_t* mask;      // optional acceptance mask
+    const double* u;          // optional Metropolis uniforms: accept if |r|^2 >= u
+};
+
 // ---- launchers (defined in lru_kernels.cu, instantiated for every dtype) ----
 template <typename T>
 void launch_propose(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& U,
@@ -87,6 +102,9 @@ void launch_form_pf_moves(const DevLayout& L, const T* F, int m, const int* pos,
 template <typename T>
 void launch_gather(bool pairs, const DevLayout& L, const T* src, int m, const int* occ, T* A, int* err,
                    cudaStream_t st);
+template <typename T>
+void launch_step(bool pf, const DevLayout& L, const DevState<T>& S, const DevOperand& U, const DevOperand& V,
+                 const T* C, T* ratio_out, int* st_out, const StepCtl& ctl, int grid, cudaStream_t st);
 template <typename T>
 void launch_zero_split_tail(const DevLayout& L, const DevState<T>& S, const uint8_t* force, cudaStream_t st);
 void launch_commit_moves(int W, int n, int* occ, const int* slot, const int* newrow, const uint8_t* mask,

@@ -91,8 +91,8 @@ struct TileIter {
 // One CTA per walker.
 // ---------------------------------------------------------------------------
 template <typename T, bool PF, bool DELAYED>
-__global__ void __launch_bounds__(PT) k_propose(DevLayout L, DevState<T> S, DevOperand U, DevOperand V,
-                                                 const T* C, T* ratio_out, int* st_out) {
+__device__ void propose_walker(const int w, const DevLayout L, const DevState<T> S, const DevOperand U,
+                               const DevOperand V, const T* C, T* ratio_out, int* st_out) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     T* s_qtu = reinterpret_cast<T*>(dyn_smem);  // Kc x MAXKK (delayed only)
     __shared__ T s_core[MAXKK * MAXKK];
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(PT) k_propose(DevLayout L, DevState<T> S, DevO
     __shared__ int s_bad;
     __shared__ T s_pfc;
 
-    const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int n = L.nw(w), kk = L.kv(w);
     const long long vo = L.vo(w);
     const T* G = S.G + L.mo(w);
@@ -379,6 +379,12 @@ __global__ void __launch_bounds__(PT) k_propose(DevLayout L, DevState<T> S, DevO
     }
 }
 
+template <typename T, bool PF, bool DELAYED>
+__global__ void __launch_bounds__(PT) k_propose(DevLayout L, DevState<T> S, DevOperand U, DevOperand V,
+                                                 const T* C, T* ratio_out, int* st_out) {
+    propose_walker<T, PF, DELAYED>(blockIdx.x, L, S, U, V, C, ratio_out, st_out);
+}
+
 // Q^T U for the dense U columns of the delayed propose, one CTA per walker
 // and column: QtU[w][c][a] = sum_j Q[j][c] u_a[j].  Runs before k_propose.
 template <typename T>
@@ -417,10 +423,9 @@ __global__ void __launch_bounds__(PT) k_qtu_dense(DevLayout L, DevState<T> S, De
 //   delayed: y -= (V P) Q[l,:]^T ; Q[l, tau] = (R^{-1} y)^T     (b_tau equation)
 // ---------------------------------------------------------------------------
 template <typename T, bool DELAYED, int NPL, int KKS>
-__global__ void __launch_bounds__(PT) k_accept(DevLayout L, DevState<T> S, DevOperand V, const uint8_t* mask,
-                                                const int4* items) {
+__device__ void accept_item(const int4 it, const DevLayout L, const DevState<T> S, const DevOperand V,
+                            const uint8_t* mask) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    const int4 it = items[blockIdx.x];
     const int w = it.x;
     if (mask && !mask[w]) return;
     if (S.pst[w] != 0) return;
@@ -531,6 +536,12 @@ __global__ void __launch_bounds__(PT) k_accept(DevLayout L, DevState<T> S, DevOp
             }
         }
     }
+}
+
+template <typename T, bool DELAYED, int NPL, int KKS>
+__global__ void __launch_bounds__(PT) k_accept(DevLayout L, DevState<T> S, DevOperand V, const uint8_t* mask,
+                                                const int4* items) {
+    accept_item<T, DELAYED, NPL, KKS>(items[blockIdx.x], L, S, V, mask);
 }
 
 // Delayed accept of a real rank-1 update with the GEMV in double-float
@@ -719,6 +730,106 @@ __global__ void __launch_bounds__(256) k_flush_df(DevLayout L, DevState<double> 
 }
 
 #endif
+
+// ---------------------------------------------------------------------------
+// Persistent fused step for walkers of uneven n and k: one launch of a fixed
+// grid that pulls work from a device queue,
+//   items [0, W)          : propose walker order[i] (largest n^2 k first), then
+//                           the accept decision (mask, or Metropolis |r|^2 >= u)
+//   items [W, W + nacc)   : accept items (walker, chunk range), largest first,
+// An accept item waits (bounded, acquire) for its walker's propose flag; all
+// proposes are dequeued before any accept item, so every producer is already
+// running.  The last accept item of a walker commits log|value| and the sign.
+// Counters and flags are cleared by a memset in the same stream before the
+// launch, so the pair can be captured in a CUDA graph and replayed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename T, bool PF, int NPL, int KKS>
+__global__ void __launch_bounds__(PT) k_step(DevLayout L, DevState<T> S, DevOperand U, DevOperand V, const T* C,
+                                              T* ratio_out, int* st_out, StepCtl ctl) {
+    __shared__ int s_item, s_ok;
+    const int total = L.W + (ctl.do_accept ? ctl.nacc : 0);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(ctl.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        if (item < L.W) {
+            const int w = ctl.order[item];
+            propose_walker<T, PF, false>(w, L, S, U, V, C, ratio_out, st_out);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                bool acc = ctl.do_accept && S.pst[w] == 0;
+                if (acc && ctl.mask) acc = ctl.mask[w] != 0;
+                if (acc && ctl.u) acc = (double)s_abs2(S.ratio[w]) >= ctl.u[w];
+                ctl.acc[w] = acc ? 1 : 0;
+                __threadfence();
+                st_release_gpu(&ctl.prop_done[w], 1);
+            }
+        } else {
+            const int4 it = ctl.acc_items[item - L.W];
+            const int w = it.x;
+            if (threadIdx.x == 0) {
+                int ok = 0;
+                for (long long i = 0; i < (1ll << 24); ++i) {
+                    if (ld_acquire_gpu(&ctl.prop_done[w]) == 1) { ok = 1; break; }
+                    __nanosleep(64);
+                }
+                if (!ok) set_dev_error(S.err, DEV_ERR_TIMEOUT);
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (s_ok && ctl.acc[w]) accept_item<T, false, NPL, KKS>(it, L, S, V, nullptr);
+            __syncthreads();
+            if (threadIdx.x == 0 && s_ok) {
+                __threadfence();
+                const int done = atomicAdd(&ctl.items_done[w], 1) + 1;
+                if (done == ctl.nacc_w[w] && ctl.acc[w]) {
+                    const T r = S.ratio[w];
+                    S.logabs[w] += log(s_absd(r));
+                    S.sgn[w] = s_renorm(S.sgn[w] * s_unit(r));
+                    S.pst[w] = 4;
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+void launch_step(bool pf, const DevLayout& L, const DevState<T>& S, const DevOperand& U, const DevOperand& V,
+                 const T* C, T* ratio_out, int* st_out, const StepCtl& ctl, int grid, cudaStream_t st) {
+    const int nmax = L.n_max;
+    int npl = 1;
+    while (32 * npl < nmax) npl *= 2;
+    size_t dyn = (size_t)2 * L.kk * nmax * sizeof(T);
+    if (dyn > 160 * 1024) dyn = 0;
+    const bool rank1 = L.kk == 1 && L.kvec == nullptr;
+#define LRU_STEP(N)                                                                                         \
+    case N:                                                                                                 \
+        if (pf) {                                                                                           \
+            auto k = rank1 ? k_step<T, true, N, 1> : k_step<T, true, N, 0>;                                  \
+            static bool attr = false;                                                                       \
+            if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); attr = true; } \
+            k<<<grid, PT, dyn, st>>>(L, S, U, V, C, ratio_out, st_out, ctl);                                \
+        } else {                                                                                            \
+            auto k = rank1 ? k_step<T, false, N, 1> : k_step<T, false, N, 0>;                                \
+            static bool attr = false;                                                                       \
+            if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); attr = true; } \
+            k<<<grid, PT, dyn, st>>>(L, S, U, V, C, ratio_out, st_out, ctl);                                \
+        }                                                                                                   \
+        break;
+    switch (npl) { LRU_STEP(1) LRU_STEP(2) LRU_STEP(4) LRU_STEP(8) LRU_STEP(16) LRU_STEP(32) LRU_STEP(64) default: break; }
+#undef LRU_STEP
+}
 
 // After the accept pass: log|value| += log|r|, sign *= r/|r|, tau += 1 (delayed)
 template <typename T>
@@ -1130,6 +1241,8 @@ void launch_commit_moves(int W, int n, int* occ, const int* slot, const int* new
     template void launch_flush_finish<T>(const DevLayout&, const DevState<T>&, const uint8_t*, cudaStream_t); \
     template void launch_set_delay_zero<T>(const DevLayout&, const DevState<T>&, cudaStream_t);             \
     template void launch_zero_split_tail<T>(const DevLayout&, const DevState<T>&, const uint8_t*, cudaStream_t); \
+    template void launch_step<T>(bool, const DevLayout&, const DevState<T>&, const DevOperand&, const DevOperand&, \
+                                 const T*, T*, int*, const StepCtl&, int, cudaStream_t);                      \
     template void launch_get_inverse<T>(bool, bool, const DevLayout&, const DevState<T>&, T*, cudaStream_t); \
     template void launch_form_row_moves<T>(const DevLayout&, const T*, int, const int*, const int*,         \
                                            const int*, T*, int*, cudaStream_t);                             \

@@ -55,6 +55,12 @@ struct lru_ctx {
     int* d_kv = nullptr;
     int* d_items = nullptr;
     int nitems = 0;
+    // persistent step: propose order, accept items (largest walkers first), control block
+    int* d_order = nullptr;
+    int* d_sitems = nullptr;
+    int* d_nacc_w = nullptr;
+    int* d_ctl = nullptr;        // counter, prop_done[W], items_done[W]
+    uint8_t* d_acc = nullptr;
     bool items_smem = true;
     void *G = nullptr, *P = nullptr, *Q = nullptr;
     float *P32h = nullptr, *P32l = nullptr, *Q32h = nullptr, *Q32l = nullptr;
@@ -200,6 +206,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     if (cfg->delay < 0) return LRU_ERR_ARG;
     if (cfg->flush < LRU_FLUSH_NATIVE || cfg->flush > LRU_FLUSH_DF) return LRU_ERR_ARG;
     if (cfg->arith != LRU_ARITH_NATIVE && cfg->arith != LRU_ARITH_DF) return LRU_ERR_ARG;
+    if (cfg->tile_chunks < 0) return LRU_ERR_ARG;
     const bool delayed = cfg->delay >= 2;
     if (delayed && cfg->delay * kk > MAXKC) return LRU_ERR_ARG;
     if (cfg->flush != LRU_FLUSH_NATIVE && !(delayed && cfg->dtype == LRU_F64)) return LRU_ERR_UNSUPPORTED;
@@ -266,7 +273,8 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     h->items_smem = (size_t)2 * kk * h->n_max * sz <= 160 * 1024;
     for (int w = 0; w < h->W; ++w) {
         const int n = h->n_h[w];
-        const int ch = std::max(8, std::min(64, n / 4));
+        const int ch = cfg->tile_chunks > 0 ? std::min(cfg->tile_chunks, 256)
+                                            : std::max(8, std::min(64, n / 4));
         for (int l0 = 0; l0 < n; l0 += ch) {
             items.push_back(w);
             items.push_back(l0);
@@ -275,6 +283,19 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
         }
     }
     h->nitems = (int)items.size() / 4;
+    // persistent-step queue: walkers by decreasing n^2 k (longest first)
+    std::vector<int> order(h->W), nacc_w(h->W, 0), sitems;
+    for (int w = 0; w < h->W; ++w) order[w] = w;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long long)h->n_h[a] * h->n_h[a] * h->kv_h[a] > (long long)h->n_h[b] * h->n_h[b] * h->kv_h[b];
+    });
+    for (size_t q = 0; q < items.size(); q += 4) nacc_w[items[q]] += 1;
+    {
+        std::vector<std::vector<int>> per(h->W);
+        for (size_t q = 0; q < items.size(); q += 4)
+            for (int c = 0; c < 4; ++c) per[items[q]].push_back(items[q + c]);
+        for (int w : order) sitems.insert(sitems.end(), per[w].begin(), per[w].end());
+    }
 
     // one allocation: persistent state first, then scratch and metadata
     const bool tc = delayed && cfg->flush != LRU_FLUSH_NATIVE && cfg->flush != LRU_FLUSH_DF;
@@ -300,6 +321,11 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     const size_t oVoff = take((size_t)h->W * sizeof(long long));
     const size_t oKv = take((size_t)h->W * sizeof(int));
     const size_t oItems = take(items.size() * sizeof(int));
+    const size_t oOrder = take((size_t)h->W * sizeof(int));
+    const size_t oSItems = take(sitems.size() * sizeof(int));
+    const size_t oNacc = take((size_t)h->W * sizeof(int));
+    const size_t oCtl = take((size_t)(1 + 2 * h->W) * sizeof(int));
+    const size_t oAcc = take((size_t)h->W);
     h->bytes = off;
     if (cudaMalloc(&h->base, h->bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -330,13 +356,21 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     h->d_voff = (long long*)(b + oVoff);
     h->d_kv = kuni ? nullptr : (int*)(b + oKv);
     h->d_items = (int*)(b + oItems);
+    h->d_order = (int*)(b + oOrder);
+    h->d_sitems = (int*)(b + oSItems);
+    h->d_nacc_w = (int*)(b + oNacc);
+    h->d_ctl = (int*)(b + oCtl);
+    h->d_acc = (uint8_t*)(b + oAcc);
     lru_status s = LRU_OK;
     if (cudaMemset(h->base, 0, h->bytes) != cudaSuccess ||
         cudaMemcpy(h->d_n, h->n_h.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_moff, h->moff_h.data(), h->W * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_voff, h->voff_h.data(), h->W * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b + oKv, h->kv_h.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(h->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(h->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_order, order.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_sitems, sitems.data(), sitems.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_nacc_w, nacc_w.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
         s = LRU_ERR_CUDA;
     if (s != LRU_OK) {
         cudaGetLastError();
@@ -467,6 +501,44 @@ lru_status lru_propose_pf(lru_handle h, const lru_operand* B, const void* C, voi
     lru_status s = cuda_check();
     if (s != LRU_OK) return s;
     h->lastV = dB;
+    h->lastC = C;
+    h->has_prop = true;
+    return LRU_OK;
+}
+
+lru_status lru_step_persistent(lru_handle h, const lru_operand* U, const lru_operand* V, const void* C,
+                               int32_t accept, const uint8_t* mask, const double* u, void* ratio, int32_t* st,
+                               uint8_t* acc_out) {
+    if (!h || !ratio) return LRU_ERR_ARG;
+    if (h->delayed) return LRU_ERR_UNSUPPORTED;
+    if (!operand_ok(U, h->kk)) return LRU_ERR_ARG;
+    if (!h->pf && !operand_ok(V, h->kk)) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    DevOperand dU{U->dense, U->idx, U->onehot_mask, h->kk};
+    DevOperand dV = h->pf ? dU : DevOperand{V->dense, V->idx, V->onehot_mask, h->kk};
+    StepCtl ctl;
+    ctl.counter = h->d_ctl;
+    ctl.prop_done = h->d_ctl + 1;
+    ctl.items_done = h->d_ctl + 1 + h->W;
+    ctl.acc = acc_out ? acc_out : h->d_acc;
+    ctl.order = h->d_order;
+    ctl.acc_items = reinterpret_cast<const int4*>(h->d_sitems);
+    ctl.nacc_w = h->d_nacc_w;
+    ctl.nacc = h->nitems;
+    ctl.do_accept = accept != 0;
+    ctl.mask = mask;
+    ctl.u = u;
+    CK(cudaMemsetAsync(h->d_ctl, 0, (size_t)(1 + 2 * h->W) * sizeof(int), h->stream));
+    DevLayout L = h->layout();
+    h->launches += 1;
+    prof_begin(h, LRU_PROF_PROPOSE);
+    LRU_DISPATCH(h, {
+        launch_step<T>(h->pf, L, h->state<T>(), dU, dV, (const T*)C, (T*)ratio, st, ctl, 2 * h->n_sm, h->stream);
+    });
+    prof_end(h, LRU_PROF_PROPOSE);
+    lru_status s = cuda_check();
+    if (s != LRU_OK) return s;
+    h->lastV = dV;
     h->lastC = C;
     h->has_prop = true;
     return LRU_OK;

@@ -51,7 +51,7 @@ class _Config(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("walkers", C.c_int64), ("n", C.c_int32),
                 ("n_per_walker", C.POINTER(C.c_int32)), ("k", C.c_int32),
                 ("k_per_walker", C.POINTER(C.c_int32)), ("delay", C.c_int32), ("flush", C.c_int32),
-                ("device", C.c_int32), ("arith", C.c_int32)]
+                ("device", C.c_int32), ("arith", C.c_int32), ("tile_chunks", C.c_int32)]
 
 
 class _Operand(C.Structure):
@@ -71,6 +71,7 @@ _SIGS = {
     "lru_propose_det": [_H, C.POINTER(_Operand), C.POINTER(_Operand), _vp, _vp],
     "lru_propose_pf": [_H, C.POINTER(_Operand), _vp, _vp, _vp],
     "lru_accept": [_H, _vp],
+    "lru_step_persistent": [_H, C.POINTER(_Operand), C.POINTER(_Operand), _vp, _i32, _vp, _vp, _vp, _vp, _vp],
     "lru_flush_delayed": [_H, _vp],
     "lru_get_inverse": [_H, _vp],
     "lru_get_logvalue": [_H, _vp, _vp],
@@ -168,7 +169,7 @@ class LowRankState:
 
     def __init__(self, kind: str, walkers: int, n, k: int = 1, dtype=torch.float64, delay: int = 0,
                  flush: int = FLUSH_NATIVE, k_per_walker=None, device: Optional[int] = None,
-                 arith: int = ARITH_NATIVE):
+                 arith: int = ARITH_NATIVE, tile_chunks: int = 0):
         self.kind = {"det": DET, "pf": PF}[kind]
         self.dtype = dtype
         self.W = int(walkers)
@@ -199,6 +200,7 @@ class LowRankState:
         cfg.flush = int(flush)
         cfg.device = dev
         cfg.arith = int(arith)
+        cfg.tile_chunks = int(tile_chunks)
         h = _H()
         _check(_lib.lru_create(C.byref(cfg), C.byref(h)), "lru_create")
         self._h = h
@@ -255,6 +257,22 @@ class LowRankState:
         b = B._c()
         _check(_lib.lru_propose_pf(self._h, C.byref(b), _ptr(Cmat), _ptr(ratio), _ptr(status)), "lru_propose_pf")
         return ratio, status
+
+    def step_persistent(self, U: Operand, V: Optional[Operand] = None, Cmat: Optional[torch.Tensor] = None,
+                        accept: bool = True, mask=None, u=None, ratio=None, status=None, acc=None):
+        """One persistent fused propose(+accept) launch over all walkers (ragged n, k
+        allowed); graph-capturable.  Returns (ratio, status, accepted)."""
+        self._bind()
+        ratio = self._vec_out(self.dtype) if ratio is None else ratio
+        status = torch.empty(self.W, dtype=torch.int32, device=self.device) if status is None else status
+        acc = torch.empty(self.W, dtype=torch.uint8, device=self.device) if acc is None else acc
+        self._last = (U, V, Cmat)
+        u_c = U._c()
+        v_c = (V or U)._c()
+        _check(_lib.lru_step_persistent(self._h, C.byref(u_c), C.byref(v_c), _ptr(Cmat), 1 if accept else 0,
+                                        _mask_ptr(mask), _ptr(u), _ptr(ratio), _ptr(status), _ptr(acc)),
+               "lru_step_persistent")
+        return ratio, status, acc
 
     def accept(self, mask: Optional[torch.Tensor] = None):
         self._bind()
@@ -320,34 +338,44 @@ class LowRankState:
         _check(_lib.lru_log_ratio(self._h, _ptr(out)), "lru_log_ratio")
         return out
 
+    @property
+    def uniform(self) -> bool:
+        return len(set(self.n_list)) == 1
+
     def _ops_like(self):
-        n = self.n_list[0]
-        return torch.zeros(self.W, self.kmax, n, dtype=self.dtype, device=self.device)
+        """Zeros in the operand vector layout: (W, kmax, n), or flat sum(n) * kmax when n varies."""
+        if self.uniform:
+            return torch.zeros(self.W, self.kmax, self.n_list[0], dtype=self.dtype, device=self.device)
+        return torch.zeros(sum(self.n_list) * self.kmax, dtype=self.dtype, device=self.device)
+
+    def _mats_like(self):
+        """Matrices of every walker: (W, n, n), or flat sum(n^2) when n varies."""
+        if self.uniform:
+            n = self.n_list[0]
+            return torch.empty(self.W, n, n, dtype=self.dtype, device=self.device)
+        return torch.empty(sum(x * x for x in self.n_list), dtype=self.dtype, device=self.device)
 
     def backward_det(self, g: torch.Tensor, want_U=True, want_V=True, want_A=True):
         """(gU, gV, gA): vector-Jacobian product of the pending proposal's log ratio."""
         self._bind()
-        n = self.n_list[0]
         gU = self._ops_like() if want_U else None
         gV = self._ops_like() if want_V else None
-        gA = torch.empty(self.W, n, n, dtype=self.dtype, device=self.device) if want_A else None
+        gA = self._mats_like() if want_A else None
         _check(_lib.lru_backward_det(self._h, _ptr(g.contiguous()), _ptr(gU), _ptr(gV), _ptr(gA)), "lru_backward_det")
         return gU, gV, gA
 
     def backward_pf(self, g: torch.Tensor, want_B=True, want_C=True, want_A=True):
         """(gB, gC, gA) for the pending Pfaffian proposal (skew parts of A and C)."""
         self._bind()
-        n = self.n_list[0]
         gB = self._ops_like() if want_B else None
         gC = torch.empty(self.W, self.kmax, self.kmax, dtype=self.dtype, device=self.device) if want_C else None
-        gA = torch.empty(self.W, n, n, dtype=self.dtype, device=self.device) if want_A else None
+        gA = self._mats_like() if want_A else None
         _check(_lib.lru_backward_pf(self._h, _ptr(g.contiguous()), _ptr(gB), _ptr(gC), _ptr(gA)), "lru_backward_pf")
         return gB, gC, gA
 
     def backward_logvalue(self, g: torch.Tensor) -> torch.Tensor:
         self._bind()
-        n = self.n_list[0]
-        gA = torch.empty(self.W, n, n, dtype=self.dtype, device=self.device)
+        gA = self._mats_like()
         _check(_lib.lru_backward_logvalue(self._h, _ptr(g.contiguous()), _ptr(gA)), "lru_backward_logvalue")
         return gA
 
