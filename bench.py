@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--m", type=int, default=2048)
     p.add_argument("--delay", type=int, default=16)
     p.add_argument("--refresh-every", type=int, default=128)
-    p.add_argument("--arms", default="plain,delayed,delayed_tf32x3",
+    p.add_argument("--arms", default="plain,delayed,delayed_tf32x3,delayed_dfgemv",
                    help="comma list of " + ",".join(ARMS))
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -142,9 +142,10 @@ ARITH = {"native": 0, "df": 1}
 
 # name -> (delay, arith, flush); "delayed" is the headline form
 ARMS = {
-    "plain": (0, "native", "native"),
-    "delayed": (None, "df", "df"),
-    "delayed_tf32x3": (None, "df", "tf32x3"),
+    "plain": (0, "native", "native"),              # FP64 Sherman-Morrison step (Eq. det_inv)
+    "delayed": (None, "native", "df"),             # FP64 GEMV, double-float flush
+    "delayed_tf32x3": (None, "native", "tf32x3"),  # FP64 GEMV, tensor-core TF32x3 flush (precision form)
+    "delayed_dfgemv": (None, "df", "df"),          # double-float GEMV and flush
 }
 
 

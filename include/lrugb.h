@@ -232,11 +232,14 @@ lru_status lru_scatter_rows_add(lru_handle h, const void* gA, const int32_t* row
 
 /* ---- operand formation for QMC moves (Sec. 2.2, 3.2) --------------------- */
 
-/* Determinant row replacement: walker w moves slot i = slot[w] from orbital
- * row occ[w][i] to row new_row[w] of Phi (m x n row-major, shared by all
- * walkers).  Writes V_out (kmax = 1 vector layout) = Phi[new] - Phi[occ_i]
- * and idx_out[w] = i, so U = e_i (one-hot) and V = V_out (dense).  occ is W x n
- * int32 and is not changed.  Uniform-n handles only. */
+/* Determinant row replacement (Sec. 2.2, Eq. det_rank1_row; k > 1: k rows at
+ * once, e.g. two-electron moves): walker w moves slot i_a = slot[w*k + a]
+ * from orbital row occ[w][i_a] to row new_row[w*k + a] of Phi (m x n
+ * row-major, shared by all walkers), a < k.  Writes V_out (vector layout,
+ * kmax = k) with row a = Phi[new_a] - Phi[occ_{i_a}] and idx_out[w*k + a] =
+ * i_a, so U = [e_{i_a}] (one-hot) and V = V_out (dense).  Slots and new rows
+ * of one walker must be distinct.  occ is W x n int32 and is not changed.
+ * Uniform-n handles only. */
 lru_status lru_form_row_moves(lru_handle h, const void* Phi, int32_t m, const int32_t* occ,
                               const int32_t* slot, const int32_t* new_row,
                               void* V_out, int32_t* idx_out);
@@ -248,8 +251,9 @@ lru_status lru_form_row_moves(lru_handle h, const void* Phi, int32_t m, const in
 lru_status lru_form_pf_moves(lru_handle h, const void* F, int32_t m, const int32_t* pos,
                              const int32_t* slot, const int32_t* new_site,
                              void* B_out, int32_t* idx_out);
-/* After an accept: occ[w][slot[w]] = new_row[w] for masked walkers whose
- * proposal status was OK (mask NULL = all). */
+/* After an accept: occ[w][slot[w*k + a]] = new_row[w*k + a] (a < k; k = 1 for
+ * Pfaffian handles) for masked walkers whose proposal was accepted (mask
+ * NULL = all). */
 lru_status lru_commit_moves(lru_handle h, int32_t* occ, const int32_t* slot,
                             const int32_t* new_row, const uint8_t* mask);
 

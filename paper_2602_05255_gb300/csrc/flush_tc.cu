@@ -28,8 +28,8 @@ namespace lru {
 
 constexpr int TC_THREADS = 256;
 constexpr int TILE = 128;         // M = N = 128
-constexpr int KCHUNK = 32;        // TF32 elements per 128-byte swizzle row
-constexpr int CHUNK_BYTES = TILE * KCHUNK * 4;   // 16 KiB per operand per K chunk
+constexpr int ROW_BYTES = 128;    // one 128-byte swizzle row per tile row and K chunk
+constexpr int CHUNK_BYTES = TILE * ROW_BYTES;    // 16 KiB per operand per K chunk
 constexpr uint32_t TMEM_COLS = 128;
 
 struct TcMaps {
@@ -85,16 +85,29 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
     return d;
 }
 
-// instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, M = N = 128
+// instruction descriptors: D f32, A and B K-major, M = N = 128;
+// kind::tf32 (A/B format 2 = TF32) and kind::f16 (A/B format 1 = BF16)
 constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TILE >> 3) << 17) |
                                 ((uint32_t)(TILE >> 4) << 24);
+constexpr uint32_t IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TILE >> 3) << 17) |
+                                ((uint32_t)(TILE >> 4) << 24);
 
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-        ::"r"(dtmem), "l"(a), "l"(b), "r"(IDESC_TF32), "r"(acc)
-        : "memory");
+// one MMA step of K = 32 bytes of each row (8 TF32 or 16 BF16 elements)
+template <bool BF16>
+__device__ __forceinline__ void mma_step(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+    if constexpr (BF16) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(dtmem), "l"(a), "l"(b), "r"(IDESC_BF16), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(dtmem), "l"(a), "l"(b), "r"(IDESC_TF32), "r"(acc)
+            : "memory");
+    }
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -127,10 +140,11 @@ __device__ __forceinline__ double f2d_int(float f) {
 
 // One CTA per SM slot, persistent over the (walker, tile) list of the walkers
 // that flush now.  Walker w flushes when tau_w >= K (or force[w] and tau_w > 0).
-template <bool PF>
+template <bool PF, bool BF16>
 __global__ void __launch_bounds__(TC_THREADS, 2)
     k_flush_tc(const __grid_constant__ TcMaps maps, DevLayout L, double* G, const int* tau, const uint8_t* force,
                int nkc, int three, int* err) {
+    constexpr int KCHUNK = BF16 ? 64 : 32;   // elements per 128-byte row
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // 1024-byte aligned operand area: [Ph | Pl | Qh | Ql] x nkc chunks
@@ -213,14 +227,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                         const uint64_t bh = desc_sw128(smem_u32(sQh + kc * CHUNK_BYTES));
                         const uint64_t bl = desc_sw128(smem_u32(sQl + kc * CHUNK_BYTES));
 #pragma unroll
-                        for (int ks = 0; ks < KCHUNK / 8; ++ks) {
-                            const uint64_t adv = (uint64_t)(ks * 32) >> 4;   // 8 TF32 = 32 bytes along K
+                        for (int ks = 0; ks < ROW_BYTES / 32; ++ks) {
+                            const uint64_t adv = (uint64_t)(ks * 32) >> 4;   // 32 bytes along K per MMA
                             if (three) {
-                                mma_tf32(tmem, al + adv, bh + adv, acc);
+                                mma_step<BF16>(tmem, al + adv, bh + adv, acc);
                                 acc = 1;
-                                mma_tf32(tmem, ah + adv, bl + adv, 1);
+                                mma_step<BF16>(tmem, ah + adv, bl + adv, 1);
                             }
-                            mma_tf32(tmem, ah + adv, bh + adv, acc);
+                            mma_step<BF16>(tmem, ah + adv, bh + adv, acc);
                             acc = 1;
                         }
                     }
@@ -313,52 +327,60 @@ static EncodeTiled get_encode() {
     return fn;
 }
 
-// rows x cols float matrix (row-major, cols = Kc_pad), box 32 x 128, SWIZZLE_128B
-static bool make_map(CUtensorMap* m, const float* base, long long rows, int cols) {
+// rows x cols matrix (row-major, cols = Kc_pad) of fp32 or bf16, box
+// (128 bytes) x 128 rows, SWIZZLE_128B
+static bool make_map(CUtensorMap* m, const void* base, long long rows, int cols, bool bf16) {
     EncodeTiled enc = get_encode();
     if (!enc) return false;
+    const size_t es_bytes = bf16 ? 2 : 4;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)TILE};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * es_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / es_bytes), (cuuint32_t)TILE};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base,
+                     dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-bool launch_flush_tc(int mode, bool pf, const DevLayout& L, double* G, const float* Ph, const float* Pl,
-                     const float* Qh, const float* Ql, const int* tau, const uint8_t* force_mask, int* err,
+bool launch_flush_tc(int mode, bool pf, const DevLayout& L, double* G, const void* Ph, const void* Pl,
+                     const void* Qh, const void* Ql, const int* tau, const uint8_t* force_mask, int* err,
                      cudaStream_t st) {
-    // mode: 1 = TF32x3, 2 = TF32 (BF16 modes are not built)
-    if (mode != 1 && mode != 2) return false;
-    if (L.Kc32 <= 0 || L.Kc32 % KCHUNK) return false;
-    static thread_local const float* cached[4] = {nullptr, nullptr, nullptr, nullptr};
+    // mode: 1 = TF32x3, 2 = TF32, 3 = BF16, 4 = BF16x3
+    if (mode < 1 || mode > 4) return false;
+    const bool bf16 = mode >= 3;
+    const int kchunk = bf16 ? 64 : 32;
+    if (L.Kc32 <= 0 || L.Kc32 % kchunk) return false;
+    static thread_local const void* cached[4] = {nullptr, nullptr, nullptr, nullptr};
     static thread_local long long cached_rows = -1;
-    static thread_local int cached_cols = -1;
+    static thread_local int cached_cols = -1, cached_bf16 = -1;
     static thread_local TcMaps maps;
     if (cached[0] != Ph || cached[1] != Pl || cached[2] != Qh || cached[3] != Ql || cached_rows != L.rows ||
-        cached_cols != L.Kc32) {
-        if (!make_map(&maps.ph, Ph, L.rows, L.Kc32) || !make_map(&maps.pl, Pl, L.rows, L.Kc32) ||
-            !make_map(&maps.qh, Qh, L.rows, L.Kc32) || !make_map(&maps.ql, Ql, L.rows, L.Kc32))
+        cached_cols != L.Kc32 || cached_bf16 != (int)bf16) {
+        if (!make_map(&maps.ph, Ph, L.rows, L.Kc32, bf16) || !make_map(&maps.pl, Pl, L.rows, L.Kc32, bf16) ||
+            !make_map(&maps.qh, Qh, L.rows, L.Kc32, bf16) || !make_map(&maps.ql, Ql, L.rows, L.Kc32, bf16))
             return false;
         cached[0] = Ph; cached[1] = Pl; cached[2] = Qh; cached[3] = Ql;
         cached_rows = L.rows;
         cached_cols = L.Kc32;
+        cached_bf16 = (int)bf16;
     }
-    const int nkc = L.Kc32 / KCHUNK;
+    const int nkc = L.Kc32 / kchunk;
     const size_t dyn = 1024 + (size_t)4 * nkc * CHUNK_BYTES + (pf ? (size_t)8 * 32 * 33 * sizeof(double) : 0);
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    auto kern = pf ? k_flush_tc<true> : k_flush_tc<false>;
+    auto kern = pf ? (bf16 ? k_flush_tc<true, true> : k_flush_tc<true, false>)
+                   : (bf16 ? k_flush_tc<false, true> : k_flush_tc<false, false>);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     // two CTAs per SM (2 x 128 TMEM columns): one streams its epilogue while
     // the other waits on TMA and the MMAs
-    kern<<<2 * nsm, TC_THREADS, dyn, st>>>(maps, L, G, tau, force_mask, nkc, mode == 1 ? 1 : 0, err);
+    const int three = (mode == 1 || mode == 4) ? 1 : 0;
+    kern<<<2 * nsm, TC_THREADS, dyn, st>>>(maps, L, G, tau, force_mask, nkc, three, err);
     return true;
 }
 

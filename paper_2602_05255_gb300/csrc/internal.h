@@ -20,7 +20,7 @@ struct DevLayout {
     const int* kvec;           // per-walker vector count, or nullptr (= kk)
     int Kc;                    // delay columns per walker row of P, Q (K * kk), 0 if plain
     int K;                     // delay length (>= 2 for the delayed form)
-    int Kc32;                  // row stride of the FP32 split copies (Kc rounded up to 32)
+    int Kc32;                  // row stride (elements) of the split copies: Kc rounded up to 32 (TF32) or 64 (BF16)
     long long rows;            // sum of n over walkers (rows of P, Q)
     __device__ __forceinline__ int nw(int w) const { return n_uni > 0 ? n_uni : n[w]; }
     __device__ __forceinline__ long long mo(int w) const {
@@ -38,7 +38,8 @@ struct DevState {
     T* G;          // A^{-1} (plain) or A_0^{-1} (delayed), column-major per walker
     T* P;          // delayed: n_w x Kc per walker, row j contiguous
     T* Q;
-    float* P32h;   // delayed, tensor-core flush: split copies of P and Q (K-major)
+    int split_bf16;  // 0: the split copies are TF32 in fp32 words; 1: bf16
+    float* P32h;   // delayed, tensor-core flush: split copies of P and Q (K-major rows of Kc32)
     float* P32l;
     float* Q32h;
     float* Q32l;
@@ -107,7 +108,7 @@ void launch_step(bool pf, const DevLayout& L, const DevState<T>& S, const DevOpe
                  const T* C, T* ratio_out, int* st_out, const StepCtl& ctl, int grid, cudaStream_t st);
 template <typename T>
 void launch_zero_split_tail(const DevLayout& L, const DevState<T>& S, const uint8_t* force, cudaStream_t st);
-void launch_commit_moves(int W, int n, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
+void launch_commit_moves(int W, int n, int k, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
                          const int* pst, cudaStream_t st);
 template <typename T>
 void launch_set_delay_zero(const DevLayout& L, const DevState<T>& S, cudaStream_t st);
@@ -141,8 +142,8 @@ void launch_scatter_rows(const DevLayout& L, const T* gA, const int* rows, int m
 
 // ---- tensor-core flush (flush_tc.cu) ----
 // Returns false when the combination is not built.
-bool launch_flush_tc(int mode, bool pf, const DevLayout& L, double* G, const float* Ph, const float* Pl,
-                     const float* Qh, const float* Ql, const int* tau, const uint8_t* force_mask,
+bool launch_flush_tc(int mode, bool pf, const DevLayout& L, double* G, const void* Ph, const void* Pl,
+                     const void* Qh, const void* Ql, const int* tau, const uint8_t* force_mask,
                      int* err, cudaStream_t st);
 
 }  // namespace lru

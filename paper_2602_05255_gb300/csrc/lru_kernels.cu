@@ -10,6 +10,8 @@
 #include "small_core.cuh"
 #include "df.cuh"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <type_traits>
 
@@ -31,6 +33,26 @@ __device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
     float xf = (float)x;
     hi = tf32_round(xf);
     lo = tf32_round((float)(x - (double)hi));
+}
+
+// store the hi / lo split of x at element o of the split copies (TF32 in fp32
+// words, or bf16); PQ selects the P (0) or Q (1) arrays
+template <typename T>
+__device__ __forceinline__ void store_split(const DevState<T>& S, int PQ, long long o, double x) {
+    float* h = PQ ? S.Q32h : S.P32h;
+    float* l = PQ ? S.Q32l : S.P32l;
+    if (S.split_bf16) {
+        const float xf = (float)x;
+        const __nv_bfloat16 bh = __float2bfloat16_rn(xf);
+        const __nv_bfloat16 bl = __float2bfloat16_rn((float)(x - (double)__bfloat162float(bh)));
+        reinterpret_cast<__nv_bfloat16*>(h)[o] = bh;
+        reinterpret_cast<__nv_bfloat16*>(l)[o] = bl;
+    } else {
+        float hi, lo;
+        split_tf32(x, hi, lo);
+        h[o] = hi;
+        l[o] = lo;
+    }
 }
 
 template <typename T>
@@ -250,13 +272,7 @@ __device__ void propose_walker(const int w, const DevLayout L, const DevState<T>
                     T x = X[(long long)a * n + j];
                     S.P[off] = x;
                     if constexpr (!traits<T>::is_complex && sizeof(T) == 8) {
-                        if (S.P32h) {
-                            const long long o32 = (vo + j) * L.Kc32 + cu + a;
-                            float h, lo;
-                            split_tf32((double)x, h, lo);
-                            S.P32h[o32] = h;
-                            S.P32l[o32] = lo;
-                        }
+                        if (S.P32h) store_split(S, 0, (vo + j) * L.Kc32 + cu + a, (double)x);
                     }
                 }
             }
@@ -365,13 +381,8 @@ __device__ void propose_walker(const int w, const DevLayout L, const DevState<T>
                 if constexpr (!traits<T>::is_complex && sizeof(T) == 8) {
                     if (S.P32h) {
                         const long long o32 = (vo + j) * L.Kc32 + cu + b;
-                        float h, lo;
-                        split_tf32((double)p, h, lo);
-                        S.P32h[o32] = h;
-                        S.P32l[o32] = lo;
-                        split_tf32((double)q, h, lo);
-                        S.Q32h[o32] = h;
-                        S.Q32l[o32] = lo;
+                        store_split(S, 0, o32, (double)p);
+                        store_split(S, 1, o32, (double)q);
                     }
                 }
             }
@@ -525,13 +536,7 @@ __device__ void accept_item(const int4 it, const DevLayout L, const DevState<T> 
                 const long long off = (vo + l) * Kc + cu + lane;
                 S.Q[off] = zz;
                 if constexpr (!traits<T>::is_complex && sizeof(T) == 8) {
-                    if (S.P32h) {
-                        const long long o32 = (vo + l) * L.Kc32 + cu + lane;
-                        float h, lo;
-                        split_tf32((double)zz, h, lo);
-                        S.Q32h[o32] = h;
-                        S.Q32l[o32] = lo;
-                    }
+                    if (S.P32h) store_split(S, 1, (vo + l) * L.Kc32 + cu + lane, (double)zz);
                 }
             }
         }
@@ -625,13 +630,7 @@ __global__ void __launch_bounds__(PT, 3) k_accept_delayed_df(DevLayout L, DevSta
             const double y = df_to_double(ah0, al0) - sCorr[l - it.y];
             const double z = rinv * y;
             S.Q[(vo + l) * Kc + cu] = z;
-            if (S.P32h) {
-                const long long o32 = (vo + l) * L.Kc32 + cu;
-                float h, lo;
-                split_tf32(z, h, lo);
-                S.Q32h[o32] = h;
-                S.Q32l[o32] = lo;
-            }
+            if (S.P32h) store_split(S, 1, (vo + l) * L.Kc32 + cu, z);
         }
     }
 }
@@ -965,8 +964,13 @@ __global__ void k_zero_split_tail(DevLayout L, DevState<T> S, const uint8_t* for
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * width;
          e += (long long)gridDim.x * blockDim.x) {
         const long long off = (vo + e / width) * L.Kc32 + cu + e % width;
-        S.P32h[off] = 0.f;
-        S.P32l[off] = 0.f;
+        if (S.split_bf16) {
+            reinterpret_cast<__nv_bfloat16*>(S.P32h)[off] = __float2bfloat16_rn(0.f);
+            reinterpret_cast<__nv_bfloat16*>(S.P32l)[off] = __float2bfloat16_rn(0.f);
+        } else {
+            S.P32h[off] = 0.f;
+            S.P32l[off] = 0.f;
+        }
     }
 }
 
@@ -1021,15 +1025,19 @@ __global__ void __launch_bounds__(256) k_get_inverse(DevLayout L, DevState<T> S,
 template <typename T>
 __global__ void k_form_row_moves(DevLayout L, const T* Phi, int m, const int* occ, const int* slot,
                                  const int* newrow, T* Vout, int* idx) {
-    const int w = blockIdx.x, n = L.n_uni;
-    const int i = slot[w];
-    const bool ok_i = i >= 0 && i < n;
-    const int nr = newrow[w];
-    const int old = ok_i ? occ[(long long)w * n + i] : 0;
-    const bool ok = ok_i && nr >= 0 && nr < m && old >= 0 && old < m;
-    for (int j = threadIdx.x; j < n; j += blockDim.x)
-        Vout[(long long)w * n + j] = ok ? (Phi[(long long)nr * n + j] - Phi[(long long)old * n + j]) : s_zero(T());
-    if (threadIdx.x == 0) idx[w] = ok ? i : -1;   // -1 is rejected by propose
+    // k simultaneous moves per walker: slot[w*k + a] -> new_row[w*k + a]
+    const int w = blockIdx.x, n = L.n_uni, k = L.kk;
+    for (int a = 0; a < k; ++a) {
+        const int i = slot[(long long)w * k + a];
+        const bool ok_i = i >= 0 && i < n;
+        const int nr = newrow[(long long)w * k + a];
+        const int old = ok_i ? occ[(long long)w * n + i] : 0;
+        const bool ok = ok_i && nr >= 0 && nr < m && old >= 0 && old < m;
+        T* vo = Vout + ((long long)w * k + a) * n;
+        for (int j = threadIdx.x; j < n; j += blockDim.x)
+            vo[j] = ok ? (Phi[(long long)nr * n + j] - Phi[(long long)old * n + j]) : s_zero(T());
+        if (threadIdx.x == 0) idx[(long long)w * k + a] = ok ? i : -1;   // -1 is rejected by propose
+    }
 }
 
 template <typename T>
@@ -1084,14 +1092,16 @@ void launch_gather(bool pairs, const DevLayout& L, const T* src, int m, const in
 }
 
 #if !defined(LRU_INST_DTYPE) || defined(LRU_INST_PRIMARY)
-__global__ void k_commit_moves(int W, int n, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
-                               const int* pst) {
+__global__ void k_commit_moves(int W, int n, int k, int* occ, const int* slot, const int* newrow,
+                               const uint8_t* mask, const int* pst) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= W) return;
     if (mask && !mask[w]) return;
     if (pst && pst[w] != 4) return;   // 4: consumed by an accept
-    const int i = slot[w];
-    if (i >= 0 && i < n) occ[(long long)w * n + i] = newrow[w];
+    for (int a = 0; a < k; ++a) {
+        const int i = slot[(long long)w * k + a];
+        if (i >= 0 && i < n) occ[(long long)w * n + i] = newrow[(long long)w * k + a];
+    }
 }
 #endif
 
@@ -1225,9 +1235,9 @@ void launch_form_pf_moves(const DevLayout& L, const T* F, int m, const int* pos,
 }
 
 #if !defined(LRU_INST_DTYPE) || defined(LRU_INST_PRIMARY)
-void launch_commit_moves(int W, int n, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
+void launch_commit_moves(int W, int n, int k, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
                          const int* pst, cudaStream_t st) {
-    k_commit_moves<<<(W + 255) / 256, 256, 0, st>>>(W, n, occ, slot, newrow, mask, pst);
+    k_commit_moves<<<(W + 255) / 256, 256, 0, st>>>(W, n, k, occ, slot, newrow, mask, pst);
 }
 #endif
 

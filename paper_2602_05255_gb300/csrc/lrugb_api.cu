@@ -39,6 +39,7 @@ struct lru_ctx {
     int dtype = 0;
     bool pf = false, delayed = false;
     int W = 0, kk = 0, K = 0, Kc = 0, Kc32 = 0, flush = 0;
+    bool split_bf16 = false;
     bool df = false;
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -108,6 +109,7 @@ struct lru_ctx {
         S.G = (T*)G;
         S.P = (T*)P;
         S.Q = (T*)Q;
+        S.split_bf16 = split_bf16 ? 1 : 0;
         S.P32h = P32h;
         S.P32l = P32l;
         S.Q32h = Q32h;
@@ -210,7 +212,6 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     const bool delayed = cfg->delay >= 2;
     if (delayed && cfg->delay * kk > MAXKC) return LRU_ERR_ARG;
     if (cfg->flush != LRU_FLUSH_NATIVE && !(delayed && cfg->dtype == LRU_F64)) return LRU_ERR_UNSUPPORTED;
-    if (cfg->flush == LRU_FLUSH_BF16 || cfg->flush == LRU_FLUSH_BF16X3) return LRU_ERR_UNSUPPORTED;
     if (cfg->flush == LRU_FLUSH_DF && !(delayed && cfg->dtype == LRU_F64)) return LRU_ERR_UNSUPPORTED;
 
     lru_ctx* h = new (std::nothrow) lru_ctx();
@@ -225,7 +226,9 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     h->kk = kk;
     h->K = delayed ? cfg->delay : 0;
     h->Kc = delayed ? cfg->delay * kk : 0;
-    h->Kc32 = (h->Kc + 31) / 32 * 32;
+    const bool bf16 = cfg->flush == LRU_FLUSH_BF16 || cfg->flush == LRU_FLUSH_BF16X3;
+    h->split_bf16 = bf16;
+    h->Kc32 = bf16 ? (h->Kc + 63) / 64 * 64 : (h->Kc + 31) / 32 * 32;
     h->flush = cfg->flush;
     h->device = cfg->device;
     h->df = cfg->arith == LRU_ARITH_DF && cfg->dtype == LRU_F64;
@@ -304,7 +307,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     const size_t oG = take((size_t)h->sum_n2 * sz);
     const size_t oP = delayed ? take((size_t)h->sum_n * h->Kc * sz) : 0;
     const size_t oQ = delayed ? take((size_t)h->sum_n * h->Kc * sz) : 0;
-    const size_t o32 = tc ? take((size_t)4 * h->sum_n * h->Kc32 * sizeof(float)) : 0;
+    const size_t o32 = tc ? take((size_t)4 * h->sum_n * h->Kc32 * (h->split_bf16 ? 2 : sizeof(float))) : 0;
     const size_t oTau = take((size_t)h->W * sizeof(int));
     const size_t oLog = take((size_t)h->W * sizeof(double));
     const size_t oSgn = take((size_t)h->W * sz);
@@ -336,11 +339,11 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     h->G = b + oG;
     if (delayed) { h->P = b + oP; h->Q = b + oQ; }
     if (tc) {
-        const size_t e = (size_t)h->sum_n * h->Kc32;
+        const size_t e = (size_t)h->sum_n * h->Kc32 * (h->split_bf16 ? 2 : sizeof(float));   // bytes
         h->P32h = (float*)(b + o32);
-        h->P32l = h->P32h + e;
-        h->Q32h = h->P32l + e;
-        h->Q32l = h->Q32h + e;
+        h->P32l = (float*)(b + o32 + e);
+        h->Q32h = (float*)(b + o32 + 2 * e);
+        h->Q32l = (float*)(b + o32 + 3 * e);
     }
     h->tau = (int*)(b + oTau);
     h->logabs = (double*)(b + oLog);
@@ -658,7 +661,7 @@ lru_status lru_check_device_error(lru_handle h) {
 lru_status lru_form_row_moves(lru_handle h, const void* Phi, int32_t m, const int32_t* occ, const int32_t* slot,
                               const int32_t* new_row, void* V_out, int32_t* idx_out) {
     if (!h || !Phi || !occ || !slot || !new_row || !V_out || !idx_out || m < 1) return LRU_ERR_ARG;
-    if (h->pf || h->n_uni <= 0 || h->kk != 1) return LRU_ERR_ARG;
+    if (h->pf || h->n_uni <= 0) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     DevLayout L = h->layout();
     h->launches += 1;
@@ -687,7 +690,7 @@ lru_status lru_commit_moves(lru_handle h, int32_t* occ, const int32_t* slot, con
     if (h->n_uni <= 0) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     h->launches += 1;
-    launch_commit_moves(h->W, h->n_uni, occ, slot, new_row, mask, h->pst, h->stream);
+    launch_commit_moves(h->W, h->n_uni, h->pf ? 1 : h->kk, occ, slot, new_row, mask, h->pst, h->stream);
     return cuda_check();
 }
 

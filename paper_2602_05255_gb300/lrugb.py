@@ -407,8 +407,8 @@ class LowRankState:
     def form_row_moves(self, Phi, occ, slot, new_row, V_out=None, idx_out=None):
         self._bind()
         n = self.n_list[0]
-        V_out = torch.empty(self.W, 1, n, dtype=self.dtype, device=self.device) if V_out is None else V_out
-        idx_out = torch.empty(self.W, 1, dtype=torch.int32, device=self.device) if idx_out is None else idx_out
+        V_out = torch.empty(self.W, self.k, n, dtype=self.dtype, device=self.device) if V_out is None else V_out
+        idx_out = torch.empty(self.W, self.k, dtype=torch.int32, device=self.device) if idx_out is None else idx_out
         _check(_lib.lru_form_row_moves(self._h, _ptr(Phi), Phi.shape[0], _ptr(occ), _ptr(slot), _ptr(new_row),
                                        _ptr(V_out), _ptr(idx_out)), "lru_form_row_moves")
         return V_out, idx_out

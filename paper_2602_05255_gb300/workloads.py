@@ -78,6 +78,31 @@ def move_sequence(seed: int, occ0: np.ndarray, m: int, steps: int):
     return slot, new
 
 
+def multi_move_sequence(seed: int, occ0: np.ndarray, m: int, steps: int, k: int):
+    """k simultaneous moves per step (e.g. two-electron moves, k = 2): k
+    distinct slots and k distinct unoccupied rows, every move assumed
+    accepted.  Returns (slot, new), each steps x walkers x k int32."""
+    g = rng(seed)
+    W, n = occ0.shape
+    occ = occ0.astype(np.int64).copy()
+    occupied = np.zeros((W, m), dtype=bool)
+    occupied[np.arange(W)[:, None], occ] = True
+    free = np.stack([np.flatnonzero(~occupied[w]) for w in range(W)])
+    rows = np.arange(W)
+    slot = np.empty((steps, W, k), dtype=np.int32)
+    new = np.empty((steps, W, k), dtype=np.int32)
+    for s in range(steps):
+        sl = np.argsort(g.random((W, n)), axis=1)[:, :k]
+        pk = np.argsort(g.random((W, m - n)), axis=1)[:, :k]
+        for a in range(k):
+            nr = free[rows, pk[:, a]]
+            free[rows, pk[:, a]] = occ[rows, sl[:, a]]
+            occ[rows, sl[:, a]] = nr
+            slot[s, :, a] = sl[:, a]
+            new[s, :, a] = nr
+    return slot, new
+
+
 def dense_operands(seed: int, walkers: int, n: int, k: int, var: float, complex_: bool = False):
     """Dense backflow-style operands: U (walkers x k x n, column a of U stored
     as a length-n vector) and V (walkers x k x n, row a of V)."""

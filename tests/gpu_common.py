@@ -31,7 +31,7 @@ def check_ratios(gpu, chain, exact, base=RTOL_F64, what="", eps_scale=1.0):
     max(base, 10 * eps_scale * e) where e = |r_chain - r_exact| / |r_exact| is
     the oracle chain's own FP64 rounding error against the from-scratch ratio
     (large after a near-node step); eps_scale is the unit roundoff of the GPU
-    arithmetic over FP64's (64 for double-float, 2^-47 / 2^-53).  Near-node
+    arithmetic over FP64's (256 for the double-float paths).  Near-node
     steps (|r_exact| < 1e-6 median |r|) compare absolute errors against
     base * median |r|."""
     gpu, chain, exact = (np.asarray(x) for x in (gpu, chain, exact))

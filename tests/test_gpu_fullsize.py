@@ -1,0 +1,262 @@
+"""Every workload configuration at its full size on the GPU, checked on
+sampled walkers against the CPU oracle (walkers are independent, so a sampled
+walker's chain is the oracle's chain for those inputs).
+
+- det, 4096 walkers, n = 512, Phi 1024 x 512 N(0, 1/n), FP64 and complex128,
+  rank-1 row moves, delay K = 16, 256 steps, refresh every 128 steps;
+- pf, 1024 walkers, n = 256 on 512 sites, F = G - G^T with G N(0, 1/n),
+  row-and-column moves, K = 8, 256 steps, FP64 and complex128;
+- precision form, 64 walkers, n = 2048, Phi 4096 x 2048, two-electron moves
+  (k = 2), K = 32, flush in TF32x3 / BF16 on the tensor cores, FP64 small
+  core, log/sign and refresh every 64 steps: drift against the FP64 chain;
+- uneven batching, 2048 walkers with n in {128, 256, 512, 1024} and k in
+  {1, 2, 4, 8}, backflow-style dense U, V, complex64 / complex128, one
+  persistent launch, adjoint against central finite differences (h = 1e-6).
+Exact ratios for the condition-aware bound come from LAPACK slogdet.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import O, check_ratios, fro_rel, lrugb, rel, tdev, torch
+from paper_2602_05255_gb300 import workloads
+
+GO = pytest.importorskip("oracle.grad_oracle")
+
+pytestmark = pytest.mark.gpu
+
+
+def exact_det_ratio(A, U, V):
+    s1, l1 = np.linalg.slogdet(A + U @ V)
+    s0, l0 = np.linalg.slogdet(A)
+    return s1 / s0 * math.exp(l1 - l0)
+
+
+# (dtype, GEMV arithmetic, flush): FP64 end to end at the 1e-10 bar; the
+# double-float options at their own bound (DF_SCALE); complex128 in FP64
+CASES = [("f64", 0, 0), ("f64", 1, 5), ("c128", 0, 0)]
+# products of two double-float splits have unit roundoff 2^-46 against FP64's
+# 2^-53, and a chain applies two of them (GEMV and flush): 2^8 x FP64's error
+DF_SCALE = 256.0
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_det_4096_walkers_n512(case):
+    L = lrugb()
+    dt, arith, flush = case
+    cplx = dt == "c128"
+    W, n, m, steps, K, every = 4096, 512, 1024, 256, 16, 128
+    seed = 2
+    tdt = torch.complex128 if cplx else torch.float64
+    Phi = workloads.orbital_matrix(seed, m, n, 1.0 / n, cplx)
+    occ0 = workloads.initial_occupation(seed + 1, W, m, n)
+    slot, new = workloads.move_sequence(seed + 2, occ0, m, steps)
+    st = L.LowRankState("det", W, n, k=1, dtype=tdt, delay=K, flush=flush, arith=arith)
+    Phi_d, occ_d = tdev(Phi, tdt), tdev(occ0)
+    A_d = st.gather_rows(Phi_d, occ_d)
+    st.init(A_d)
+    sample = [0, 1777, W - 1]
+    ratios = np.zeros((steps, len(sample)), dtype=np.complex128 if cplx else np.float64)
+    slot_d, new_d = tdev(slot), tdev(new)
+    for s in range(steps):
+        V, idx = st.form_row_moves(Phi_d, occ_d, slot_d[s], new_d[s])
+        r, status = st.propose_det(L.Operand(idx=idx, onehot_mask=1), L.Operand(dense=V))
+        st.accept()
+        st.commit_moves(occ_d, slot_d[s], new_d[s])
+        ratios[s] = r[sample].cpu().numpy()
+        if (s + 1) % every == 0:
+            st.gather_rows(Phi_d, occ_d, A_d)
+            st.refresh(A_d, want_drift=False)
+    inv = st.inverse()[sample].cpu().numpy()
+    st.check_device_error()
+    scale = DF_SCALE if (arith == L.ARITH_DF or flush == L.FLUSH_DF) else 1.0
+    for q, w in enumerate(sample):
+        occ = occ0[w].copy()
+        Ainv = np.linalg.inv(O.slater_matrix(Phi, occ))
+        chain, exact = [], []
+        for s in range(steps):
+            U, V = O.det_row_move(Phi, occ, slot[s, w], new[s, w])
+            exact.append(exact_det_ratio(O.slater_matrix(Phi, occ), U, V))
+            r, Ainv = O.det_lru(Ainv, U, V, return_update=True)
+            chain.append(r)
+            occ[slot[s, w]] = new[s, w]
+            if (s + 1) % every == 0:
+                Ainv = np.linalg.inv(O.slater_matrix(Phi, occ))
+        check_ratios(ratios[:, q], chain, exact, what=w, eps_scale=scale)
+        assert fro_rel(inv[q], np.linalg.inv(O.slater_matrix(Phi, occ))) <= 1e-10 * scale
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_pf_1024_walkers_n256(case):
+    L = lrugb()
+    dt, _, flush = case
+    cplx = dt == "c128"
+    W, n, m, steps, K = 1024, 256, 512, 256, 8
+    seed = 3
+    tdt = torch.complex128 if cplx else torch.float64
+    G = workloads.pairing_generator(seed, m, 1.0 / n, cplx)
+    F = G - G.T
+    pos0 = workloads.initial_occupation(seed + 1, W, m, n)
+    slot, new = workloads.move_sequence(seed + 2, pos0, m, steps)
+    st = L.LowRankState("pf", W, n, k=1, dtype=tdt, delay=K, flush=flush)
+    F_d, pos_d = tdev(F, tdt), tdev(pos0)
+    st.init(st.gather_pairs(F_d, pos_d))
+    sample = [0, 511, W - 1]
+    ratios = np.zeros((steps, len(sample)), dtype=np.complex128 if cplx else np.float64)
+    slot_d, new_d = tdev(slot), tdev(new)
+    for s in range(steps):
+        B, idx = st.form_pf_moves(F_d, pos_d, slot_d[s], new_d[s])
+        r, _ = st.propose_pf(L.Operand(dense=B, idx=idx, onehot_mask=0b10))
+        st.accept()
+        st.commit_moves(pos_d, slot_d[s], new_d[s])
+        ratios[s] = r[sample].cpu().numpy()
+    inv = st.inverse()[sample].cpu().numpy()
+    logabs, _ = st.logvalue()
+    logabs = logabs[sample].cpu().numpy()
+    st.check_device_error()
+    scale = DF_SCALE if flush == L.FLUSH_DF else 1.0
+    for q, w in enumerate(sample):
+        pos = pos0[w].copy()
+        car = O.init_pf_carrier(O.pairing_matrix(F, pos), K)
+        l0 = np.linalg.slogdet(O.pairing_matrix(F, pos))[1] / 2
+        chain, exact = [], []
+        for s in range(steps):
+            B, C = O.pf_row_col_move(F, pos, slot[s, w], new[s, w])
+            A0 = O.pairing_matrix(F, pos)
+            chain.append(O.pf_lru_delayed(car, B, C))
+            pos[slot[s, w]] = new[s, w]
+            A1 = O.pairing_matrix(F, pos)
+            # |pf A1 / pf A0| from LAPACK (pf^2 = det), sign / phase from the chain
+            mag = math.exp((np.linalg.slogdet(A1)[1] - np.linalg.slogdet(A0)[1]) / 2)
+            exact.append(chain[-1] / abs(chain[-1]) * mag)
+        check_ratios(ratios[:, q], chain, exact, what=w, eps_scale=scale)
+        A = O.pairing_matrix(F, pos)
+        assert fro_rel(inv[q], np.linalg.inv(A)) <= 1e-10 * scale
+        l1 = np.linalg.slogdet(A)[1] / 2
+        assert abs(logabs[q] - l1) <= 1e-9 * max(1.0, abs(l1))
+
+
+def test_precision_form_n2048_two_electron_moves():
+    L = lrugb()
+    W, n, m, steps, K, every = 64, 2048, 4096, 256, 32, 64
+    seed = 4
+    Phi = workloads.orbital_matrix(seed, m, n, 1.0 / n)
+    occ0 = workloads.initial_occupation(seed + 1, W, m, n)
+    slot, new = workloads.multi_move_sequence(seed + 2, occ0, m, steps, 2)
+    Phi_d, slot_d, new_d = tdev(Phi), tdev(slot), tdev(new)
+    out = {}
+    for name, flush, arith in (("fp64", L.FLUSH_DF, L.ARITH_DF), ("tf32x3", L.FLUSH_TF32X3, L.ARITH_DF),
+                               ("bf16x3", L.FLUSH_BF16X3, L.ARITH_DF), ("bf16", L.FLUSH_BF16, L.ARITH_DF)):
+        st = L.LowRankState("det", W, n, k=2, dtype=torch.float64, delay=K, flush=flush, arith=arith)
+        occ_d = tdev(occ0)
+        A_d = st.gather_rows(Phi_d, occ_d)
+        st.init(A_d)
+        rs = torch.empty(steps, W, dtype=torch.float64, device="cuda")
+        for s in range(steps):
+            V, idx = st.form_row_moves(Phi_d, occ_d, slot_d[s], new_d[s])
+            st.propose_det(L.Operand(idx=idx, onehot_mask=0b11), L.Operand(dense=V), ratio=rs[s])
+            st.accept()
+            st.commit_moves(occ_d, slot_d[s], new_d[s])
+            if (s + 1) % every == 0:
+                st.gather_rows(Phi_d, occ_d, A_d)
+                st.refresh(A_d, want_drift=False)
+        out[name] = rs.cpu().numpy()
+        st.check_device_error()
+        st.close()
+    # the FP64-class chain against the oracle on a sampled walker (first 64 steps)
+    w = 5
+    occ = occ0[w].copy()
+    Ainv = np.linalg.inv(O.slater_matrix(Phi, occ))
+    chain, exact = [], []
+    for s in range(64):
+        U = O.onehot_matrix(n, slot[s, w])
+        V = np.stack([Phi[new[s, w, a]] - Phi[occ[slot[s, w, a]]] for a in range(2)])
+        exact.append(exact_det_ratio(O.slater_matrix(Phi, occ), U, V))
+        r, Ainv = O.det_lru(Ainv, U, V, return_update=True)
+        chain.append(r)
+        occ[slot[s, w]] = new[s, w]
+    check_ratios(out["fp64"][:64, w], chain, exact, what=w, eps_scale=64.0)
+    # drift of the reduced-precision flushes against the FP64-class chain (all walkers, all steps)
+    ref = out["fp64"]
+    med = np.median(np.abs(ref))
+    gate = np.abs(ref) >= 1e-6 * med
+    drift = {k: float(np.median(np.abs(v - ref)[gate] / np.abs(ref)[gate])) for k, v in out.items() if k != "fp64"}
+    print("precision-form median ratio drift vs FP64:", drift)
+    # orders of the flush arithmetic, amplified by the conditioning of the Slater chains
+    assert drift["tf32x3"] <= 1e-4 and drift["bf16x3"] <= 1e-2 and drift["bf16"] <= 1.0
+    assert drift["tf32x3"] <= drift["bf16x3"] <= drift["bf16"]
+
+
+@pytest.mark.parametrize("cplx_dtype", ["c128", "c64"])
+def test_uneven_batch_2048_walkers_persistent_and_adjoint(cplx_dtype):
+    L = lrugb()
+    tdt = torch.complex128 if cplx_dtype == "c128" else torch.complex64
+    npdt = np.complex128 if cplx_dtype == "c128" else np.complex64
+    tol = 1e-9 if cplx_dtype == "c128" else 2e-3
+    W = 2048
+    g = workloads.rng(5)
+    n_w = g.choice([128, 256, 512, 1024], W)
+    k_w = g.choice([1, 2, 4, 8], W)
+    kmax = 8
+    offs = np.concatenate([[0], np.cumsum(n_w)])
+    moffs = np.concatenate([[0], np.cumsum(n_w.astype(np.int64) ** 2)])
+    st = L.LowRankState("det", W, [int(x) for x in n_w], k=kmax, dtype=tdt, k_per_walker=[int(x) for x in k_w])
+    # A_w = 2.5 I + N(0, 1/n) (complex), built on the device
+    A = torch.empty(int(moffs[-1]), dtype=tdt, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    for w in range(W):
+        nn = int(n_w[w])
+        blk = (torch.randn(nn, nn, dtype=tdt, device="cuda", generator=gen) / math.sqrt(nn)
+               + 2.5 * torch.eye(nn, dtype=tdt, device="cuda"))
+        A[moffs[w]:moffs[w + 1]] = blk.reshape(-1)
+    st.init(A)
+    Uf = torch.zeros(int(offs[-1]) * kmax, dtype=tdt, device="cuda")
+    Vf = torch.zeros_like(Uf)
+    for w in range(W):
+        nn, kk_ = int(n_w[w]), int(k_w[w])
+        base = int(offs[w]) * kmax
+        Uf[base: base + kk_ * nn] = torch.randn(kk_ * nn, dtype=tdt, device="cuda", generator=gen) / math.sqrt(nn)
+        Vf[base: base + kk_ * nn] = torch.randn(kk_ * nn, dtype=tdt, device="cuda", generator=gen) / math.sqrt(nn)
+    # one persistent launch (propose only), captured and replayed as a CUDA graph
+    ratio = torch.empty(W, dtype=tdt, device="cuda")
+    status = torch.empty(W, dtype=torch.int32, device="cuda")
+    acc = torch.empty(W, dtype=torch.uint8, device="cuda")
+    st.step_persistent(L.Operand(dense=Uf), L.Operand(dense=Vf), accept=False, ratio=ratio, status=status, acc=acc)
+    r_eager = ratio.clone()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        st.step_persistent(L.Operand(dense=Uf), L.Operand(dense=Vf), accept=False, ratio=ratio, status=status,
+                           acc=acc)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(ratio, r_eager) and (status == 0).all()
+    gvec = (torch.randn(W, dtype=tdt, device="cuda", generator=gen))
+    gU, gV, gA = st.backward_det(gvec)
+    st.check_device_error()
+    # sampled walkers: ratio and gradients against the FP64 reference, FD on the smallest
+    sample = [int(np.argmin(n_w)), int(np.argmax(n_w * k_w)), 17]
+    for w in sample:
+        nn, kk_ = int(n_w[w]), int(k_w[w])
+        base = int(offs[w]) * kmax
+        Aw = A[moffs[w]:moffs[w + 1]].reshape(nn, nn).cpu().numpy().astype(np.complex128)
+        Uw = Uf[base: base + kk_ * nn].reshape(kk_, nn).cpu().numpy().astype(np.complex128)
+        Vw = Vf[base: base + kk_ * nn].reshape(kk_, nn).cpu().numpy().astype(np.complex128)
+        ref = exact_det_ratio(Aw, Uw.T, Vw)
+        assert rel(ratio[w].item(), ref) <= tol
+        gw = complex(gvec[w].item())
+        rA, rU, rV = GO.vjp(GO.det_log_ratio, [torch.tensor(Aw), torch.tensor(Uw.T), torch.tensor(Vw)], gw)
+        gUw = gU[base: base + kk_ * nn].reshape(kk_, nn).cpu().numpy()
+        gVw = gV[base: base + kk_ * nn].reshape(kk_, nn).cpu().numpy()
+        gAw = gA[moffs[w]:moffs[w + 1]].reshape(nn, nn).cpu().numpy()
+        assert fro_rel(gUw, rU.numpy().T) <= tol and fro_rel(gVw, rV.numpy()) <= tol
+        assert fro_rel(gAw, rA.numpy()) <= tol
+        if w == sample[0] and cplx_dtype == "c128":
+            # central finite differences (h = 1e-6) of Re(conj(g) log r) along a random U direction
+            h = 1e-6
+            D = (g.standard_normal((kk_, nn)) + 1j * g.standard_normal((kk_, nn)))
+            f = lambda Uc: (np.conj(gw) * np.log(exact_det_ratio(Aw, Uc.T, Vw))).real
+            fd = (f(Uw + h * D) - f(Uw - h * D)) / (2 * h)
+            an = np.real(np.sum(np.conj(gUw) * D))
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
