@@ -176,7 +176,7 @@ def test_precision_form_n2048_two_electron_moves():
         r, Ainv = O.det_lru(Ainv, U, V, return_update=True)
         chain.append(r)
         occ[slot[s, w]] = new[s, w]
-    check_ratios(out["fp64"][:64, w], chain, exact, what=w, eps_scale=64.0)
+    check_ratios(out["fp64"][:64, w], chain, exact, what=w, eps_scale=DF_SCALE)
     # drift of the reduced-precision flushes against the FP64-class chain (all walkers, all steps)
     ref = out["fp64"]
     med = np.median(np.abs(ref))
