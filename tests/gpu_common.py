@@ -28,20 +28,21 @@ def check_ratios(gpu, chain, exact, base=RTOL_F64, what="", eps_scale=1.0):
     """Ratio parity with a condition-aware bound.
 
     A step compares GPU and oracle-chain ratios with relative tolerance
-    max(base, 10 * eps_scale * e) where e = |r_chain - r_exact| / |r_exact| is
-    the oracle chain's own FP64 rounding error against the from-scratch ratio
-    (large after a near-node step); eps_scale is the unit roundoff of the GPU
+    max(base, 10 * eps_scale * e) where e is the largest |r_chain - r_exact| /
+    |r_exact| so far: the oracle chain's own accumulated FP64 rounding error
+    against the from-scratch ratios (large after near-node steps); eps_scale is the unit roundoff of the GPU
     arithmetic over FP64's (256 for the double-float paths).  Near-node
     steps (|r_exact| < 1e-6 median |r|) compare absolute errors against
     base * median |r|."""
     gpu, chain, exact = (np.asarray(x) for x in (gpu, chain, exact))
     med = np.median(np.abs(exact))
+    e_run = 0.0   # rounding errors accumulate along a chain: the running maximum sets the scale
     for s in range(len(exact)):
         if abs(exact[s]) < 1e-6 * med:
             assert abs(gpu[s] - chain[s]) <= base * med, (what, s, gpu[s], chain[s], exact[s])
             continue
-        e = abs(chain[s] - exact[s]) / abs(exact[s])
-        tol = max(base, 10 * eps_scale * e)
+        e_run = max(e_run, abs(chain[s] - exact[s]) / abs(exact[s]))
+        tol = max(base, 10 * eps_scale * e_run)
         assert abs(gpu[s] - chain[s]) <= tol * abs(chain[s]), (what, s, gpu[s], chain[s], exact[s], tol)
 
 

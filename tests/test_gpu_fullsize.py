@@ -72,17 +72,17 @@ def test_det_4096_walkers_n512(case):
     st.check_device_error()
     scale = DF_SCALE if (arith == L.ARITH_DF or flush == L.FLUSH_DF) else 1.0
     for q, w in enumerate(sample):
+        # the oracle's delayed chain (Sec. 2.3) with the same refresh schedule
         occ = occ0[w].copy()
-        Ainv = np.linalg.inv(O.slater_matrix(Phi, occ))
+        car = O.init_det_carrier(O.slater_matrix(Phi, occ), K)
         chain, exact = [], []
         for s in range(steps):
             U, V = O.det_row_move(Phi, occ, slot[s, w], new[s, w])
             exact.append(exact_det_ratio(O.slater_matrix(Phi, occ), U, V))
-            r, Ainv = O.det_lru(Ainv, U, V, return_update=True)
-            chain.append(r)
+            chain.append(O.det_lru_delayed(car, U, V))
             occ[slot[s, w]] = new[s, w]
             if (s + 1) % every == 0:
-                Ainv = np.linalg.inv(O.slater_matrix(Phi, occ))
+                car = O.init_det_carrier(O.slater_matrix(Phi, occ), K)
         check_ratios(ratios[:, q], chain, exact, what=w, eps_scale=scale)
         assert fro_rel(inv[q], np.linalg.inv(O.slater_matrix(Phi, occ))) <= 1e-10 * scale
 
