@@ -211,6 +211,18 @@ def run_arm(L, torch, args, arm, Phi_d, occ0, slot_d, new_d, rank, world, dist):
     return ratios_all, ms, clk, launches, prof, tau, (delay, arith, flush)
 
 
+def refresh_roofline(prof, n, W):
+    """Gauss-Jordan inverse: n^3 FMA = 2 n^3 flop per walker, FP64 pipe."""
+    ms, cnt = prof["refresh"]
+    if not cnt:
+        return None
+    ach = 2.0 * n ** 3 * W / (ms / cnt / 1e3) / 1e12
+    return {"kernel": "refresh (Gauss-Jordan inverse, FP64)", "bound": "alu", "achieved": ach,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "flop_per_launch": 2.0 * n ** 3 * W, "ms_per_launch": ms / cnt,
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (DFMA probe measured 1.06)"}
+
+
 def e2e_arm(L, torch, args, Phi_d, occ0, slot_h, new_h, steps):
     """Same metric through the C-ABI with host buffers: each step copies its
     proposals (slot, new row) host->device from pinned memory and reads the
@@ -252,6 +264,32 @@ def e2e_arm(L, torch, args, Phi_d, occ0, slot_h, new_h, steps):
     st.close()
     return {"value": W * steps / (ms / 1e3), "unit": "walker-updates/s",
             "h2d_bytes_per_step": 2 * W * 4, "d2h_bytes_per_step": W * 8, "steps": steps}
+
+
+# FP64 pipe: 152 SMs x 2 DFMA / clk x 2 flop x 2.07 GHz (the 1.25 TFLOP/s of
+# the GB300 datasheet); our DFMA probe measured 1.06 TFLOP/s at 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def exact_parity(Phi, occ0, slot, new, ratios, walkers, steps):
+    """Relative error of the GPU ratios of sampled walkers against the exact
+    ratio det(A + U V) / det(A) of every step (LAPACK slogdet on the host)."""
+    out = []
+    for w in walkers:
+        occ = occ0[w].copy()
+        for s in range(steps):
+            i, nr = slot[s, w], new[s, w]
+            A = Phi[occ]
+            A2 = A.copy()
+            A2[i] = Phi[nr]
+            s0, l0 = np.linalg.slogdet(A)
+            s1, l1 = np.linalg.slogdet(A2)
+            ex = s1 / s0 * math.exp(l1 - l0)
+            out.append(abs(ratios[s, w] - ex) / abs(ex))
+            occ[i] = nr
+    out = np.array(out)
+    return {"walkers": list(walkers), "steps": steps, "max_rel": float(out.max()),
+            "median_rel": float(np.median(out)), "p99_rel": float(np.quantile(out, 0.99))}
 
 
 def load_peaks():
@@ -308,7 +346,7 @@ def main():
              "refreshes_in_timed_region": args.steps // args.refresh_every, "refresh_ms_total": ref_ms,
              "kernel_ms": {k: v[0] for k, v in prof.items()},
              "kernel_launches_timed": {k: v[1] for k, v in prof.items()},
-             "gpu_launches": launches, "clocks": clk}
+             "gpu_launches": launches, "clocks": clk, "_prof": prof}
         # algorithmic bytes per accept launch (one walker-update of every walker):
         # plain: read + write A^{-1} (2 n^2 * 8 B); delayed: read A_0^{-1} (n^2 * 8 B)
         acc_ms, acc_n = prof["accept"]
@@ -338,14 +376,28 @@ def main():
                 "max_rel": relerr.max().item(), "median_rel": relerr.median().item(),
                 "p999_rel": relerr.float().quantile(0.999).item() if relerr.numel() < 16_000_000 else None,
                 "max_abs_over_median_abs": (d.max() / med).item(), "near_node_steps": int((~gate).sum().item())}
+    # exact parity of two sampled walkers (the first 64 timed steps)
+    if rank == 0:
+        psteps = min(args.steps, 64)
+        occ_t = occ0.copy()                      # occupation at the start of the timed region
+        for s_ in range(args.warmup):
+            occ_t[np.arange(W), slot[s_]] = new[s_]
+        for arm, r in arm_ratios.items():
+            arms[arm]["parity_vs_exact"] = exact_parity(
+                Phi, occ_t, slot[args.warmup:], new[args.warmup:], r[:psteps].cpu().numpy(), [0, W // 2], psteps)
     main_arm = "delayed" if "delayed" in arms else order[0]
     head = arms[main_arm]
     km = head["kernel_ms"]
     dom = max(km, key=lambda k: km[k])
-    roof = dict(head["accept_roofline"])
-    roof["kernel"] = "accept (GEMV / Woodbury pass over A^{-1})"
+    acc_roof = dict(head["accept_roofline"])
+    acc_roof["kernel"] = "accept (GEMV / Woodbury pass over A^{-1})"
+    acc_roof["peak_source"] = "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback"
+    ref_roof = refresh_roofline(head["_prof"], n, W) if "_prof" in head else None
+    roof = ref_roof if (dom == "refresh" and ref_roof) else acc_roof
+    roof = dict(roof)
     roof["dominant_kernel_by_time"] = dom
-    roof["peak_source"] = "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback"
+    for a in arms.values():
+        a.pop("_prof", None)
     line = {
         "metric": METRIC, "value": head["value"], "unit": "walker-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
@@ -354,7 +406,8 @@ def main():
                                f"refresh every {args.refresh_every}", "arm": main_arm,
                    "delay_K": args.delay, "walkers_per_gpu": W, "n": n, "m": m,
                    "l2": "inputs larger than L2 (A^{-1} state 8 GiB per GPU)"},
-        "roofline": roof, "arms": arms, "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+        "roofline": roof, "roofline_accept": acc_roof, "roofline_refresh": ref_roof,
+        "arms": arms, "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
     }
     if rank == 0 and not args.no_e2e:
         esteps = min(args.steps, 64)

@@ -544,8 +544,8 @@ __device__ void accept_item(const int4 it, const DevLayout L, const DevState<T> 
 }
 
 template <typename T, bool DELAYED, int NPL, int KKS>
-__global__ void __launch_bounds__(PT) k_accept(DevLayout L, DevState<T> S, DevOperand V, const uint8_t* mask,
-                                                const int4* items) {
+__global__ void __launch_bounds__(PT, 2) k_accept(DevLayout L, DevState<T> S, DevOperand V, const uint8_t* mask,
+                                                   const int4* items) {
     accept_item<T, DELAYED, NPL, KKS>(items[blockIdx.x], L, S, V, mask);
 }
 
