@@ -502,10 +502,11 @@ __device__ void accept_item(const int4 it, const DevLayout L, const DevState<T> 
                 y[b] = warp_sum(part);
             }
             if constexpr (DELAYED) {
+                // lanes split the slot sum (c = lane, lane + 32) and reduce
                 const T* qrow = S.Q + (vo + l) * Kc;
                 T corr = s_zero(T());
-                for (int c = 0; c < cu; ++c) corr = s_fma(sVP[b * 64 + c], qrow[c], corr);
-                y[b] = y[b] - corr;
+                for (int c = lane; c < cu; c += 32) corr = s_fma(sVP[b * 64 + c], qrow[c], corr);
+                y[b] = y[b] - warp_sum(corr);
             }
         }
         T z[KKS > 0 ? KKS : MAXKK];
@@ -547,6 +548,72 @@ template <typename T, bool DELAYED, int NPL, int KKS>
 __global__ void __launch_bounds__(PT, 2) k_accept(DevLayout L, DevState<T> S, DevOperand V, const uint8_t* mask,
                                                    const int4* items) {
     accept_item<T, DELAYED, NPL, KKS>(items[blockIdx.x], L, S, V, mask);
+}
+
+// Delayed accept of a rank-1 update, GEMV in the handle dtype with one THREAD
+// per column l of A_0^{-1}: the thread streams its contiguous column in
+// 16-byte loads against V (shared memory, broadcast), so the dot product
+// needs no cross-lane reduction and costs one FMA per element; it then
+// subtracts its own (V P) Q[l,:]^T correction and writes Q[l, tau] = y / r
+// (b_tau equation of Sec. 2.3).  One CTA per (walker, PT columns).
+template <typename T>
+__global__ void __launch_bounds__(PT, 2) k_accept_delayed_lane(DevLayout L, DevState<T> S, DevOperand V,
+                                                                const uint8_t* mask) {
+    __shared__ __align__(16) T sV[2048];
+    __shared__ T sVP[64];
+    const int w = blockIdx.x;
+    if (mask && !mask[w]) return;
+    if (S.pst[w] != 0) return;
+    const int n = L.nw(w);
+    const long long vo = L.vo(w);
+    const int Kc = L.Kc, cu = S.tau[w];
+    const T* vb = vec_ptr<T>(V, L, w, 0, n);
+    for (int j = threadIdx.x; j < n; j += PT) sV[j] = vb[j];
+    for (int c = threadIdx.x; c < cu; c += PT) sVP[c] = S.VP[(long long)w * MAXKK * Kc + c];
+    const T rinv = S.Rinv[(long long)w * MAXKK * MAXKK];
+    __syncthreads();
+    const int l = blockIdx.y * PT + threadIdx.x;
+    if (l >= n) return;
+    const T* __restrict__ col = S.G + L.mo(w) + (long long)l * n;
+    T acc0 = s_zero(T()), acc1 = s_zero(T());
+    if constexpr (std::is_same<T, double>::value) {
+        const double2* __restrict__ c2 = reinterpret_cast<const double2*>(col);
+        const double2* v2 = reinterpret_cast<const double2*>(sV);
+        const int np = n >> 1;
+        int p = 0;
+        for (; p + 4 <= np; p += 4) {
+            const double2 g0 = c2[p], g1 = c2[p + 1], g2 = c2[p + 2], g3 = c2[p + 3];
+            const double2 v0 = v2[p], v1 = v2[p + 1], vv2 = v2[p + 2], v3 = v2[p + 3];
+            acc0 = fma(v0.x, g0.x, acc0); acc1 = fma(v0.y, g0.y, acc1);
+            acc0 = fma(v1.x, g1.x, acc0); acc1 = fma(v1.y, g1.y, acc1);
+            acc0 = fma(vv2.x, g2.x, acc0); acc1 = fma(vv2.y, g2.y, acc1);
+            acc0 = fma(v3.x, g3.x, acc0); acc1 = fma(v3.y, g3.y, acc1);
+        }
+        for (; p < np; ++p) {
+            const double2 g = c2[p], v = v2[p];
+            acc0 = fma(v.x, g.x, acc0);
+            acc1 = fma(v.y, g.y, acc1);
+        }
+        if (n & 1) acc0 = fma(sV[n - 1], col[n - 1], acc0);
+    } else {
+        int j = 0;
+        for (; j + 4 <= n; j += 4) {
+            const T g0 = col[j], g1 = col[j + 1], g2 = col[j + 2], g3 = col[j + 3];
+            acc0 = s_fma(sV[j], g0, acc0);
+            acc1 = s_fma(sV[j + 1], g1, acc1);
+            acc0 = s_fma(sV[j + 2], g2, acc0);
+            acc1 = s_fma(sV[j + 3], g3, acc1);
+        }
+        for (; j < n; ++j) acc0 = s_fma(sV[j], col[j], acc0);
+    }
+    T y = acc0 + acc1;
+    const T* qrow = S.Q + (vo + l) * Kc;
+    for (int c = 0; c < cu; ++c) y = s_fms(sVP[c], qrow[c], y);
+    const T z = s_fma(rinv, y, s_zero(T()));
+    S.Q[(vo + l) * Kc + cu] = z;
+    if constexpr (!traits<T>::is_complex && sizeof(T) == 8) {
+        if (S.P32h) store_split(S, 1, (vo + l) * L.Kc32 + cu, (double)z);
+    }
 }
 
 // Delayed accept of a real rank-1 update with the GEMV in double-float
@@ -1169,6 +1236,13 @@ void launch_accept(bool pf, bool delayed, bool df, const DevLayout& L, const Dev
 #undef LRU_ACC_DF
                 done = true;
             }
+        }
+        if (!done && delayed && !pf && L.kk == 1 && L.kvec == nullptr && L.n_uni > 0 && !(V.mask & 1u) &&
+            L.n_uni <= 2048 && (L.n_uni % 2) == 0) {
+            // rank-1 delayed accept: one thread per column of A_0^{-1}
+            dim3 grid(L.W, (L.n_uni + PT - 1) / PT);
+            k_accept_delayed_lane<T><<<grid, PT, 0, st>>>(L, S, V, mask);
+            done = true;
         }
         if (!done) {
             if (delayed) accept_npl<T, true>(npl, L, S, V, mask, items, nitems, dyn, st);
