@@ -29,6 +29,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2602_05255_gb300 import multigpu  # noqa: E402
+
 METRIC = "walker-updates/sec at n=1024 (delayed vs plain rank-1, same GPU); roofline fraction"
 
 
@@ -202,10 +204,7 @@ def run_arm(L, torch, args, arm, Phi_d, occ0, slot_d, new_d, rank, world, dist):
     launches = st.launch_count() - launches0
     prof = {name: st.profile_read(c) for c, name in enumerate(["propose", "accept", "flush", "refresh"])}
     st.profile(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = multigpu.max_over_ranks(ms, dist, "cuda")
     tau = st.tau().cpu().numpy() if delayed else None
     st.close()
     return ratios_all, ms, clk, launches, prof, tau, (delay, arith, flush)
@@ -221,6 +220,35 @@ def refresh_roofline(prof, n, W):
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
             "flop_per_launch": 2.0 * n ** 3 * W, "ms_per_launch": ms / cnt,
             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (DFMA probe measured 1.06)"}
+
+
+def accept_roofline(delay, arith, n, W, ms, hbm):
+    """Roofline of one accept launch (one walker-update of every walker).
+
+    Algorithmic bytes: plain reads and writes A^{-1} (2 n^2 x 8 B per walker);
+    delayed reads A_0^{-1} once (n^2 x 8 B).  FP64 work of the native GEMV:
+    plain n^2 FMA for y = V A^{-1} plus n^2 for the rank-1 update, delayed
+    n^2 FMA.  The bound is whichever takes longer at its peak (HBM copy
+    bandwidth, FP64 pipe); the double-float GEMV runs on the FP32 pipe and is
+    reported against HBM.
+    """
+    bytes_per = (2 if delay < 2 else 1) * n * n * 8 * W
+    flop_per = (4 if delay < 2 else 2) * n * n * W
+    t_hbm = bytes_per / (hbm * 1e9)
+    t_fp64 = flop_per / (FP64_PEAK_TFLOPS * 1e12)
+    out = {"bytes_per_launch": bytes_per, "fp64_flop_per_launch": flop_per if arith == "native" else 0,
+           "ms_per_launch": ms, "traffic": None,
+           "hbm": {"achieved": bytes_per / (ms / 1e3) / 1e9 if ms else None, "peak": hbm, "unit": "GB/s"},
+           "time_at_hbm_peak_ms": t_hbm * 1e3, "time_at_fp64_peak_ms": t_fp64 * 1e3}
+    out["hbm"]["frac"] = out["hbm"]["achieved"] / hbm if ms else None
+    if arith == "native" and t_fp64 > t_hbm:
+        ach = flop_per / (ms / 1e3) / 1e12 if ms else None
+        out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS if ms else None})
+    else:
+        out.update({"bound": "hbm", "achieved": out["hbm"]["achieved"], "peak": hbm, "unit": "GB/s",
+                    "frac": out["hbm"]["frac"]})
+    return out
 
 
 def e2e_arm(L, torch, args, Phi_d, occ0, slot_h, new_h, steps):
@@ -302,9 +330,7 @@ def load_peaks():
 
 def main():
     args = parse()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = multigpu.rank_env()
 
     if args.impl == "reference":
         if rank != 0:
@@ -321,7 +347,7 @@ def main():
     from paper_2602_05255_gb300 import workloads
 
     W, n, m = args.walkers, args.n, args.m
-    seed = args.seed + 1000 * rank
+    seed = multigpu.shard_seed(args.seed, rank)
     Phi = workloads.orbital_matrix(seed, m, n, 1.0 / n)
     occ0 = workloads.initial_occupation(seed + 1, W, m, n)
     total = args.warmup + args.steps
@@ -340,21 +366,15 @@ def main():
         arm_ratios[arm] = ratios_all
         upd = W * args.steps * world
         ref_ms = prof["refresh"][0]
-        a = {"value": upd / (ms / 1e3), "ms_per_step": ms / args.steps,
+        a = {"value": multigpu.whole_job_rate(W * args.steps, world, ms), "ms_per_step": ms / args.steps,
              "delay_K": delay, "gemv_arith": arith, "flush": flush if delay >= 2 else None,
              "value_excl_refresh": upd / ((ms - ref_ms) / 1e3) if ms > ref_ms else None,
              "refreshes_in_timed_region": args.steps // args.refresh_every, "refresh_ms_total": ref_ms,
              "kernel_ms": {k: v[0] for k, v in prof.items()},
              "kernel_launches_timed": {k: v[1] for k, v in prof.items()},
              "gpu_launches": launches, "clocks": clk, "_prof": prof}
-        # algorithmic bytes per accept launch (one walker-update of every walker):
-        # plain: read + write A^{-1} (2 n^2 * 8 B); delayed: read A_0^{-1} (n^2 * 8 B)
         acc_ms, acc_n = prof["accept"]
-        bytes_per = (2 if delay < 2 else 1) * n * n * 8 * W
-        achieved = bytes_per / (acc_ms / acc_n / 1e3) / 1e9 if acc_n else None
-        a["accept_roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                                "frac": achieved / hbm if achieved else None, "traffic": None,
-                                "bytes_per_launch": bytes_per, "ms_per_launch": acc_ms / acc_n if acc_n else None}
+        a["accept_roofline"] = accept_roofline(delay, arith, n, W, acc_ms / acc_n if acc_n else None, hbm)
         if delay >= 2:
             fl_ms, fl_n = prof["flush"]
             nfl = args.steps // delay
@@ -391,7 +411,10 @@ def main():
     dom = max(km, key=lambda k: km[k])
     acc_roof = dict(head["accept_roofline"])
     acc_roof["kernel"] = "accept (GEMV / Woodbury pass over A^{-1})"
-    acc_roof["peak_source"] = "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback"
+    acc_roof["peak_source"] = (("derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"
+                                if acc_roof["bound"] == "alu" else "") +
+                               ("; HBM of measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                                else "; HBM of fallback"))
     ref_roof = refresh_roofline(head["_prof"], n, W) if "_prof" in head else None
     roof = ref_roof if (dom == "refresh" and ref_roof) else acc_roof
     roof = dict(roof)
