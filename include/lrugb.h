@@ -201,6 +201,13 @@ lru_status lru_save_state(lru_handle h, void* buf);
 lru_status lru_load_state(lru_handle h, const void* buf);
 /* Synchronises the stream and reports (then clears) the sticky device error. */
 lru_status lru_check_device_error(lru_handle h);
+/* Self-test of failure detection without a GPU fault: enqueues one warp that
+ * waits, with the persistent step's bounded acquire wait, on a device flag
+ * that no kernel sets.  After `polls` polls (0 .. 2^24, about 64 ns apart)
+ * the wait gives up and sets the sticky LRU_ERR_TIMEOUT, which the next
+ * lru_check_device_error returns (and clears); the handle stays usable.
+ * LRU_ERR_ARG for polls outside that range. */
+lru_status lru_wait_selftest(lru_handle h, int64_t polls);
 
 /* ---- reverse-mode differentiation (adjoint kernels) ----------------------- */
 

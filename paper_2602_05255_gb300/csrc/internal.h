@@ -108,6 +108,7 @@ void launch_step(bool pf, const DevLayout& L, const DevState<T>& S, const DevOpe
                  const T* C, T* ratio_out, int* st_out, const StepCtl& ctl, int grid, cudaStream_t st);
 template <typename T>
 void launch_zero_split_tail(const DevLayout& L, const DevState<T>& S, const uint8_t* force, cudaStream_t st);
+void launch_wait_selftest(const int* flag, long long iters, int* err, cudaStream_t st);
 void launch_commit_moves(int W, int n, int k, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
                          const int* pst, cudaStream_t st);
 template <typename T>

@@ -817,6 +817,18 @@ __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// Spins (acquire loads, 64 ns naps) until *flag == want or `iters` polls have
+// failed; on giving up it records DEV_ERR_TIMEOUT in the sticky device error
+// and returns false, so the caller skips the dependent work and returns.
+__device__ __forceinline__ bool bounded_acquire_wait(const int* flag, int want, long long iters, int* err) {
+    for (long long i = 0; i < iters; ++i) {
+        if (ld_acquire_gpu(flag) == want) return true;
+        __nanosleep(64);
+    }
+    set_dev_error(err, DEV_ERR_TIMEOUT);
+    return false;
+}
+constexpr long long STEP_WAIT_POLLS = 1ll << 24;   // >= 1 s of polling
 
 template <typename T, bool PF, int NPL, int KKS>
 __global__ void __launch_bounds__(PT) k_step(DevLayout L, DevState<T> S, DevOperand U, DevOperand V, const T* C,
@@ -844,15 +856,7 @@ __global__ void __launch_bounds__(PT) k_step(DevLayout L, DevState<T> S, DevOper
         } else {
             const int4 it = ctl.acc_items[item - L.W];
             const int w = it.x;
-            if (threadIdx.x == 0) {
-                int ok = 0;
-                for (long long i = 0; i < (1ll << 24); ++i) {
-                    if (ld_acquire_gpu(&ctl.prop_done[w]) == 1) { ok = 1; break; }
-                    __nanosleep(64);
-                }
-                if (!ok) set_dev_error(S.err, DEV_ERR_TIMEOUT);
-                s_ok = ok;
-            }
+            if (threadIdx.x == 0) s_ok = bounded_acquire_wait(&ctl.prop_done[w], 1, STEP_WAIT_POLLS, S.err) ? 1 : 0;
             __syncthreads();
             if (s_ok && ctl.acc[w]) accept_item<T, false, NPL, KKS>(it, L, S, V, nullptr);
             __syncthreads();
@@ -1342,6 +1346,18 @@ LRU_INST(double)
 LRU_INST(float)
 LRU_INST(c128)
 LRU_INST(c64)
+#endif
+
+#if !defined(LRU_INST_DTYPE) || defined(LRU_INST_PRIMARY)
+// One warp waits, with the persistent step's bounded wait, on a flag that no
+// kernel ever sets: the wait must give up after `iters` polls and leave
+// DEV_ERR_TIMEOUT for the host, with the context still usable.
+__global__ void k_wait_selftest(const int* flag, long long iters, int* err) {
+    if (threadIdx.x == 0) bounded_acquire_wait(flag, 1, iters, err);
+}
+void launch_wait_selftest(const int* flag, long long iters, int* err, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(flag, iters, err);
+}
 #endif
 
 }  // namespace lru

@@ -62,6 +62,7 @@ struct lru_ctx {
     int* d_nacc_w = nullptr;
     int* d_ctl = nullptr;        // counter, prop_done[W], items_done[W]
     uint8_t* d_acc = nullptr;
+    int* d_never = nullptr;      // a flag no kernel writes (bounded-wait self-test)
     bool items_smem = true;
     void *G = nullptr, *P = nullptr, *Q = nullptr;
     float *P32h = nullptr, *P32l = nullptr, *Q32h = nullptr, *Q32l = nullptr;
@@ -329,6 +330,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     const size_t oNacc = take((size_t)h->W * sizeof(int));
     const size_t oCtl = take((size_t)(1 + 2 * h->W) * sizeof(int));
     const size_t oAcc = take((size_t)h->W);
+    const size_t oNever = take(sizeof(int));
     h->bytes = off;
     if (cudaMalloc(&h->base, h->bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -364,6 +366,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     h->d_nacc_w = (int*)(b + oNacc);
     h->d_ctl = (int*)(b + oCtl);
     h->d_acc = (uint8_t*)(b + oAcc);
+    h->d_never = (int*)(b + oNever);
     lru_status s = LRU_OK;
     if (cudaMemset(h->base, 0, h->bytes) != cudaSuccess ||
         cudaMemcpy(h->d_n, h->n_h.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -656,6 +659,15 @@ lru_status lru_check_device_error(lru_handle h) {
     if (e == DEV_ERR_TIMEOUT) return LRU_ERR_TIMEOUT;
     if (e) return LRU_ERR_CUDA;
     return LRU_OK;
+}
+
+lru_status lru_wait_selftest(lru_handle h, int64_t polls) {
+    if (!h || polls < 0 || polls > (1ll << 24)) return LRU_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemsetAsync(h->d_never, 0, sizeof(int), h->stream));
+    h->launches += 1;
+    launch_wait_selftest(h->d_never, (long long)polls, h->err, h->stream);
+    return cuda_check();
 }
 
 lru_status lru_form_row_moves(lru_handle h, const void* Phi, int32_t m, const int32_t* occ, const int32_t* slot,

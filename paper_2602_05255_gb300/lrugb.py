@@ -80,6 +80,7 @@ _SIGS = {
     "lru_save_state": [_H, _vp],
     "lru_load_state": [_H, _vp],
     "lru_check_device_error": [_H],
+    "lru_wait_selftest": [_H, _i64],
     "lru_form_row_moves": [_H, _vp, _i32, _vp, _vp, _vp, _vp, _vp],
     "lru_form_pf_moves": [_H, _vp, _i32, _vp, _vp, _vp, _vp, _vp],
     "lru_commit_moves": [_H, _vp, _vp, _vp, _vp],
@@ -329,6 +330,11 @@ class LowRankState:
     def check_device_error(self):
         self._bind()
         _check(_lib.lru_check_device_error(self._h), "lru_check_device_error")
+
+    def wait_selftest(self, polls: int):
+        """Enqueue a bounded wait on a flag nothing sets (see lru_wait_selftest)."""
+        self._bind()
+        _check(_lib.lru_wait_selftest(self._h, int(polls)), "lru_wait_selftest")
 
     # ---- reverse mode --------------------------------------------------------
     def log_ratio(self) -> torch.Tensor:
