@@ -254,7 +254,8 @@ def accept_roofline(delay, arith, n, W, ms, hbm):
 def e2e_arm(L, torch, args, Phi_d, occ0, slot_h, new_h, steps):
     """Same metric through the C-ABI with host buffers: each step copies its
     proposals (slot, new row) host->device from pinned memory and reads the
-    ratios back, inside the timed region (headline delayed form)."""
+    ratios back, inside the timed region (headline delayed form, same steps
+    and refresh schedule as the device-timed arms)."""
     W, n = args.walkers, args.n
     delay, arith, flush = ARMS["delayed"]
     st = L.LowRankState("det", W, n, k=1, dtype=torch.float64, delay=args.delay, flush=FLUSH[flush],
@@ -433,7 +434,7 @@ def main():
         "arms": arms, "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
     }
     if rank == 0 and not args.no_e2e:
-        esteps = min(args.steps, 64)
+        esteps = args.steps      # the timed schedule, refreshes included
         line["e2e"] = e2e_arm(L, torch, args, Phi_d, occ0, slot[args.warmup:args.warmup + esteps],
                               new[args.warmup:args.warmup + esteps], esteps)
     if rank == 0 and not args.no_cpu_baseline:
