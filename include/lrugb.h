@@ -88,6 +88,19 @@ typedef enum {
                                delayed GEMV of rank-1 determinant updates uses it */
 } lru_arith;
 
+/* How init and refresh compute the FP64 inverse (F64 determinant handles):
+ * the update of each 64-column Gauss-Jordan panel on the other columns is an
+ * n x n x 64 product; LRU_REFRESH_TENSOR runs it on the BF16 tensor cores as
+ * an exact split product (7 slices of 8 bits per operand, FP64 recombination:
+ * the accuracy of an FP64 update), the panels themselves in FP64.  It applies
+ * to uniform n with n % 128 == 0, 128 <= n <= 2048, W <= 65535, and to calls
+ * that do not ask for the drift; other calls use LRU_REFRESH_FP64. */
+typedef enum {
+    LRU_REFRESH_AUTO = 0,     /* the tensor-core form where it applies */
+    LRU_REFRESH_FP64 = 1,     /* blocked Gauss-Jordan entirely on the FP64 pipe */
+    LRU_REFRESH_TENSOR = 2    /* as AUTO; lru_create fails with LRU_ERR_UNSUPPORTED where it cannot apply */
+} lru_refresh;
+
 typedef struct {
     int32_t kind;                 /* lru_kind */
     int32_t dtype;                /* lru_dtype */
@@ -102,6 +115,7 @@ typedef struct {
     int32_t arith;                /* lru_arith (F64 handles; ignored otherwise) */
     int32_t tile_chunks;          /* columns of A^{-1} per CTA work item of the accept pass
                                      (0 = default min(64, max(8, n/4))); autotuned */
+    int32_t refresh;              /* lru_refresh */
 } lru_config;
 
 /* One operand of a proposal: kmax vector slots per walker (see Conventions).

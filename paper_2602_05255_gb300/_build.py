@@ -24,6 +24,7 @@ UNITS = [
     ("lru_kernels.cu", "lru_kernels_f32.o", ["-DLRU_INST_DTYPE=float"]),
     ("lru_kernels.cu", "lru_kernels_c64.o", ["-DLRU_INST_DTYPE=c64"]),
     ("refresh.cu", "refresh.o", []),
+    ("refresh_oz.cu", "refresh_oz.o", []),
     ("flush_tc.cu", "flush_tc.o", []),
     ("adjoint.cu", "adjoint.o", []),
 ]

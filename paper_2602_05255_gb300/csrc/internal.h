@@ -108,6 +108,28 @@ void launch_step(bool pf, const DevLayout& L, const DevState<T>& S, const DevOpe
                  const T* C, T* ratio_out, int* st_out, const StepCtl& ctl, int grid, cudaStream_t st);
 template <typename T>
 void launch_zero_split_tail(const DevLayout& L, const DevState<T>& S, const uint8_t* force, cudaStream_t st);
+// ---- refresh with the trailing updates on the tensor cores (refresh_oz.cu) ----
+constexpr int OZ_B = 64;   // panel width = inner dimension of each trailing update
+constexpr int OZ_S = 7;    // BF16 slices per operand (8 bits each: 56 bits)
+struct OzWork {
+    double* M;        // W x n x n row-major working matrix (M = A^T, inverted in place)
+    int* perm;        // W x n pivot rows
+    double* logacc;   // W running log|det|
+    double* sgnacc;   // W running sign
+    int* sing;        // W zero-pivot flags
+    uint16_t* Sb;     // W x OZ_S x n x OZ_B  BF16 slices of the columns of S (panel rows of M)
+    uint16_t* Pb;     // W x OZ_S x n x OZ_B  BF16 slices of the rows of (panel - E)
+    int* eS;          // W x n  power-of-two exponents of the S columns
+    int* eP;          // W x n  power-of-two exponents of the panel rows
+};
+size_t oz_work_bytes(int W, int n);
+void oz_work_carve(OzWork& Z, void* base, int W, int n);
+void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mask, cudaStream_t st);
+void launch_oz_panel(int W, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st);
+void launch_oz_finish(int W, int n, const OzWork& Z, const DevState<double>& S, const uint8_t* mask, bool delayed,
+                      cudaStream_t st);
+bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const DevState<double>& S,
+                       const uint8_t* mask, bool delayed, int* err, cudaStream_t st);
 void launch_wait_selftest(const int* flag, long long iters, int* err, cudaStream_t st);
 void launch_commit_moves(int W, int n, int k, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
                          const int* pst, cudaStream_t st);

@@ -84,6 +84,10 @@ struct lru_ctx {
     bool has_prop = false;
     DevOperand lastV{};
     const void* lastC = nullptr;
+    // workspace of the tensor-core refresh (allocated on first use)
+    void* ozw = nullptr;
+    size_t oz_bytes = 0;
+    bool oz_ok = false;          // the tensor-core refresh applies to this handle
     // adjoint workspace (allocated on first use)
     void* bws = nullptr;
     int n_sm = 148;
@@ -210,6 +214,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     if (cfg->flush < LRU_FLUSH_NATIVE || cfg->flush > LRU_FLUSH_DF) return LRU_ERR_ARG;
     if (cfg->arith != LRU_ARITH_NATIVE && cfg->arith != LRU_ARITH_DF) return LRU_ERR_ARG;
     if (cfg->tile_chunks < 0) return LRU_ERR_ARG;
+    if (cfg->refresh < LRU_REFRESH_AUTO || cfg->refresh > LRU_REFRESH_TENSOR) return LRU_ERR_ARG;
     const bool delayed = cfg->delay >= 2;
     if (delayed && cfg->delay * kk > MAXKC) return LRU_ERR_ARG;
     if (cfg->flush != LRU_FLUSH_NATIVE && !(delayed && cfg->dtype == LRU_F64)) return LRU_ERR_UNSUPPORTED;
@@ -262,6 +267,13 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     bool kuni = true;
     for (int w = 0; w < h->W; ++w) kuni = kuni && h->kv_h[w] == kk;
     if (!uniform && h->pf) { /* ragged Pfaffian handles are allowed */ }
+    {
+        const int n = h->n_uni;
+        const bool fits = h->dtype == LRU_F64 && !h->pf && n > 0 && n % 128 == 0 && n >= 128 && n <= 2048 &&
+                          h->W <= 65535;
+        if (cfg->refresh == LRU_REFRESH_TENSOR && !fits) { delete h; return LRU_ERR_UNSUPPORTED; }
+        h->oz_ok = fits && cfg->refresh != LRU_REFRESH_FP64;
+    }
 
     if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); delete h; return LRU_ERR_CUDA; }
     {
@@ -396,6 +408,7 @@ lru_status lru_destroy(lru_handle h) {
     cudaFree(h->base);
     if (h->ws) cudaFree(h->ws);
     if (h->bws) cudaFree(h->bws);
+    if (h->ozw) cudaFree(h->ozw);
     for (auto& v : h->prof_ev)
         for (auto& e : v) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     cudaGetLastError();
@@ -411,7 +424,19 @@ lru_status lru_set_stream(lru_handle h, void* stream) {
 
 lru_status lru_device_bytes(lru_handle h, size_t* bytes) {
     if (!h || !bytes) return LRU_ERR_ARG;
-    *bytes = h->bytes + (h->ws ? (size_t)h->nws * h->n_max * h->n_max * dtype_size(h->dtype) : 0);
+    *bytes = h->bytes + (h->ws ? (size_t)h->nws * h->n_max * h->n_max * dtype_size(h->dtype) : 0) + h->oz_bytes;
+    return LRU_OK;
+}
+
+static lru_status ensure_oz(lru_ctx* h) {
+    if (h->ozw) return LRU_OK;
+    const size_t b = oz_work_bytes(h->W, h->n_uni);
+    if (cudaMalloc(&h->ozw, b) != cudaSuccess) {
+        cudaGetLastError();
+        h->ozw = nullptr;
+        return LRU_ERR_NOMEM;
+    }
+    h->oz_bytes = b;
     return LRU_OK;
 }
 
@@ -419,6 +444,30 @@ static lru_status do_init(lru_handle h, const void* A, const uint8_t* mask, doub
                           void* sign_out, bool with_ws) {
     if (!A) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
+    if (h->oz_ok && !drift) {
+        // FP64 panels + tensor-core trailing updates, in place in the state
+        lru_status s = ensure_oz(h);
+        if (s != LRU_OK) return s;
+        OzWork Z{};
+        oz_work_carve(Z, h->ozw, h->W, h->n_uni);
+        Z.M = (double*)h->G;
+        DevState<double> S = h->state<double>();
+        prof_begin(h, LRU_PROF_REFRESH);
+        const bool ok = launch_refresh_oz(h->W, h->n_uni, (const double*)A, Z, S, mask, h->delayed, h->err,
+                                          h->stream);
+        prof_end(h, LRU_PROF_REFRESH);
+        if (ok) {
+            h->launches += 2 + 4 * (h->n_uni / OZ_B);
+            s = cuda_check();
+            if (s != LRU_OK) return s;
+            if (logabs_out)
+                CK(cudaMemcpyAsync(logabs_out, h->logabs, h->W * sizeof(double), cudaMemcpyDefault, h->stream));
+            if (sign_out) CK(cudaMemcpyAsync(sign_out, h->sgn, h->W * sizeof(double), cudaMemcpyDefault, h->stream));
+            h->has_prop = false;
+            return LRU_OK;
+        }
+        cudaGetLastError();   // tensor maps unavailable: the FP64 form below
+    }
     if (with_ws || h->pf) {
         lru_status s = ensure_ws(h);
         if (s != LRU_OK) return s;

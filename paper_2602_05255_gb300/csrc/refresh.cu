@@ -70,22 +70,24 @@ struct GJSmem {
     T tile[32][33];
 };
 
+// Eliminates columns [c_lo, c_hi) of M (all rows) in panels of GB columns,
+// applying each panel's row exchanges and rank-GB transform to the other
+// columns of [j_lo, j_hi) only.  Pivot rows go to perm[k]; log|pivot| and the
+// sign/phase accumulate into the shared s_log / s_sgn, a zero pivot sets
+// s_sing.  The full inverse is c = j = [0, n); the tensor-core refresh runs it
+// on one 64-column panel at a time and updates the other columns itself.
 template <typename T>
-__device__ void gj_invert(T* M, int n, int* perm, double* logabs_out, T* sgn_out, int* singular, GJSmem<T>& sm) {
+__device__ void gj_columns(T* M, int n, int c_lo, int c_hi, int j_lo, int j_hi, int* perm, double& s_log, T& s_sgn,
+                           int& s_sing, GJSmem<T>& sm) {
     __shared__ double s_v[32];
     __shared__ int s_i[32];
     __shared__ T s_rowk[GB];
     auto& sS = sm.sS;
     auto& sPan = sm.sPan;
-    __shared__ double s_log;
-    __shared__ T s_sgn;
-    __shared__ int s_sing;
     const int tid = threadIdx.x;
-    if (tid == 0) { s_log = 0.0; s_sgn = make_real<T>(1.0); s_sing = 0; }
-    __syncthreads();
 
-    for (int k0 = 0; k0 < n; k0 += GB) {
-        const int bw = min(GB, n - k0);
+    for (int k0 = c_lo; k0 < c_hi; k0 += GB) {
+        const int bw = min(GB, c_hi - k0);
         // ---- panel ----
         for (int kc = 0; kc < bw; ++kc) {
             const int k = k0 + kc;
@@ -139,7 +141,7 @@ __device__ void gj_invert(T* M, int n, int* perm, double* logabs_out, T* sgn_out
         for (int kc = 0; kc < bw; ++kc) {
             const int k = k0 + kc, p = perm[k];
             if (p != k)
-                for (int j = tid; j < n; j += RT) {
+                for (int j = j_lo + tid; j < j_hi; j += RT) {
                     if (j >= k0 && j < k0 + bw) continue;
                     T a = M[(long long)k * n + j];
                     M[(long long)k * n + j] = M[(long long)p * n + j];
@@ -149,10 +151,10 @@ __device__ void gj_invert(T* M, int n, int* perm, double* logabs_out, T* sgn_out
         }
         // ---- rank-bw update of the other columns: M += (panel - E) S ----
         const int tx = tid & 15, ty = tid >> 4;   // 16 x 16 threads, 4 x 4 outputs each
-        for (int j0 = 0; j0 < n; j0 += 64) {
+        for (int j0 = j_lo; j0 < j_hi; j0 += 64) {
             for (int e = tid; e < GB * 64; e += RT) {
                 const int c = e / 64, jj = e % 64;
-                sS[c][jj] = (c < bw && j0 + jj < n) ? M[(long long)(k0 + c) * n + j0 + jj] : s_zero(T());
+                sS[c][jj] = (c < bw && j0 + jj < j_hi) ? M[(long long)(k0 + c) * n + j0 + jj] : s_zero(T());
             }
             __syncthreads();
             for (int i0 = 0; i0 < n; i0 += 64) {
@@ -190,7 +192,7 @@ __device__ void gj_invert(T* M, int n, int* perm, double* logabs_out, T* sgn_out
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const int j = j0 + tx * 4 + c;
-                        if (j >= n || (j >= k0 && j < k0 + bw)) continue;
+                        if (j >= j_hi || (j >= k0 && j < k0 + bw)) continue;
                         M[(long long)i * n + j] = M[(long long)i * n + j] + acc[r][c];
                     }
                 }
@@ -198,6 +200,18 @@ __device__ void gj_invert(T* M, int n, int* perm, double* logabs_out, T* sgn_out
             }
         }
     }
+}
+
+// In-place Gauss-Jordan inverse of M (see gj_columns), exchanges undone.
+template <typename T>
+__device__ void gj_invert(T* M, int n, int* perm, double* logabs_out, T* sgn_out, int* singular, GJSmem<T>& sm) {
+    __shared__ double s_log;
+    __shared__ T s_sgn;
+    __shared__ int s_sing;
+    const int tid = threadIdx.x;
+    if (tid == 0) { s_log = 0.0; s_sgn = make_real<T>(1.0); s_sing = 0; }
+    __syncthreads();
+    gj_columns(M, n, 0, n, 0, n, perm, s_log, s_sgn, s_sing, sm);
     // ---- undo the exchanges as column exchanges, last first ----
     for (int k = n - 1; k >= 0; --k) {
         const int p = perm[k];
@@ -433,6 +447,118 @@ void launch_slogdet(int W, int n, const T* A, T* ws, int nws, double* logabs, T*
     const int dyn = (int)sizeof(GJSmem<T>);
     cudaFuncSetAttribute(k_slogdet<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     k_slogdet<T><<<nws, RT, dyn, st>>>(W, n, A, ws, logabs, sgn);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 parts of the tensor-core refresh (the GEMM is in refresh_oz.cu)
+// ---------------------------------------------------------------------------
+
+// M[w] = A[w]^T through 32 x 32 tiles; grid (n/32, n/32, W), block 32 x 8
+__global__ void k_oz_load(int n, const double* A, double* M, const uint8_t* mask) {
+    __shared__ double tile[32][33];
+    const int w = blockIdx.z;
+    if (mask && !mask[w]) return;
+    const long long off = (long long)w * n * n;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32, tx = threadIdx.x;
+    for (int q = threadIdx.y; q < 32; q += 8) tile[q][tx] = A[off + (long long)(r0 + q) * n + c0 + tx];
+    __syncthreads();
+    for (int q = threadIdx.y; q < 32; q += 8) M[off + (long long)(c0 + q) * n + r0 + tx] = tile[tx][q];
+}
+
+// Panel [k0, k0 + OZ_B) of walker w: Gauss-Jordan elimination of its columns
+// over all rows (updates confined to the panel), then its row exchanges
+// applied, in pivot order, to every column outside the panel.  log|pivot|
+// and the sign carry over between panels in Z.logacc / Z.sgnacc / Z.sing.
+__global__ void __launch_bounds__(RT) k_oz_panel(int n, int k0, OzWork Z, const uint8_t* mask) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    GJSmem<double>& sm = *reinterpret_cast<GJSmem<double>*>(dsm);
+    __shared__ double s_log, s_sgn;
+    __shared__ int s_sing;
+    const int w = blockIdx.x;
+    if (mask && !mask[w]) return;
+    double* M = Z.M + (long long)w * n * n;
+    int* perm = Z.perm + (long long)w * n;
+    if (threadIdx.x == 0) {
+        s_log = k0 ? Z.logacc[w] : 0.0;
+        s_sgn = k0 ? Z.sgnacc[w] : 1.0;
+        s_sing = k0 ? Z.sing[w] : 0;
+    }
+    __syncthreads();
+    gj_columns<double>(M, n, k0, k0 + OZ_B, k0, k0 + OZ_B, perm, s_log, s_sgn, s_sing, sm);
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += RT) {
+        if (j >= k0 && j < k0 + OZ_B) continue;
+        for (int kc = 0; kc < OZ_B; ++kc) {
+            const int k = k0 + kc, p = perm[k];
+            if (p != k) {
+                const double a = M[(long long)k * n + j];
+                M[(long long)k * n + j] = M[(long long)p * n + j];
+                M[(long long)p * n + j] = a;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        Z.logacc[w] = s_log;
+        Z.sgnacc[w] = s_sgn;
+        Z.sing[w] = s_sing;
+    }
+}
+
+// Undo the row exchanges of the elimination as one column permutation of
+// the inverse (idx composes the swaps, last first: M'[i][c] = M[i][idx[c]]),
+// four rows at a time through shared memory; then log|det|, sign and the
+// fresh-state flags.
+__global__ void __launch_bounds__(RT) k_oz_finish(int n, OzWork Z, DevState<double> S, const uint8_t* mask,
+                                                  bool delayed) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    double* buf = reinterpret_cast<double*>(dsm);
+    int* idx = reinterpret_cast<int*>(buf + 4 * n);
+    const int w = blockIdx.x;
+    if (mask && !mask[w]) return;
+    const int* perm = Z.perm + (long long)w * n;
+    for (int c = threadIdx.x; c < n; c += RT) idx[c] = c;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = n - 1; k >= 0; --k) {
+            const int p = perm[k];
+            if (p != k) { const int t = idx[k]; idx[k] = idx[p]; idx[p] = t; }
+        }
+    __syncthreads();
+    double* M = Z.M + (long long)w * n * n;
+    for (int i0 = 0; i0 < n; i0 += 4) {
+        const int rows = min(4, n - i0);
+        for (int e = threadIdx.x; e < rows * n; e += RT) buf[e] = M[(long long)i0 * n + e];
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * n; e += RT) {
+            const int r = e / n, c = e % n;
+            M[(long long)(i0 + r) * n + c] = buf[r * n + idx[c]];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int sing = Z.sing[w];
+        S.logabs[w] = sing ? -INFINITY : Z.logacc[w];
+        S.sgn[w] = sing ? 0.0 : s_renorm(Z.sgnacc[w]);
+        if (delayed) S.tau[w] = 0;
+        S.pst[w] = sing ? 1 : 5;
+    }
+}
+
+void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mask, cudaStream_t st) {
+    k_oz_load<<<dim3(n / 32, n / 32, W), dim3(32, 8), 0, st>>>(n, A, M, mask);
+}
+
+void launch_oz_panel(int W, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st) {
+    const int dyn = (int)sizeof(GJSmem<double>);
+    cudaFuncSetAttribute(k_oz_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    k_oz_panel<<<W, RT, dyn, st>>>(n, k0, Z, mask);
+}
+
+void launch_oz_finish(int W, int n, const OzWork& Z, const DevState<double>& S, const uint8_t* mask, bool delayed,
+                      cudaStream_t st) {
+    const int dyn = (int)(4 * n * sizeof(double) + n * sizeof(int));
+    cudaFuncSetAttribute(k_oz_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    k_oz_finish<<<W, RT, dyn, st>>>(n, Z, S, mask, delayed);
 }
 
 #define LRU_INST_R(T)                                                                                       \

@@ -1,0 +1,341 @@
+// From-scratch FP64 inverse with the trailing updates on the tensor cores.
+//
+// The refresh (Sec. 2.3 init_det_carrier; Sec. 1 advises double precision) is
+// a blocked Gauss-Jordan inversion of M = A^T, n^3 FMAs per walker, and
+// GB300's FP64 pipe runs at about 1/64 of its FP32 rate.  Panels of OZ_B = 64
+// columns are eliminated in FP64 (refresh.cu: n * 64^2 FMAs per panel); the
+// update of every other column by the panel,
+//     M[i, j] += sum_c (Pan - E)[i, c] * S[c, j],   S = rows k0 .. k0+63 of M,
+// (n^2 * 64 FMAs per panel: 94% of the work at n = 1024) runs as an
+// error-free split product on the BF16 tensor cores, the scheme of Ozaki,
+// Ogita, Oishi and Rump (Numer. Algorithms 59, 2012):
+//   - every 64-vector (a row of Pan - E, a column of S) is scaled by a power
+//     of two 2^E with |x| < 2^E and rounded to a multiple of 2^(E-56), then
+//     written exactly as 7 signed base-256 digits, x = 2^E sum_t d_t 2^(-8(t+1))
+//     (|d_0| <= 256, |d_t| <= 128), each digit times its power a BF16 value;
+//     this uses integer operations only;
+//   - the product of digit t of S and digit u of Pan has level l = t + u + 2:
+//     an integer times 2^(-8l).  Summed over the 64-wide inner dimension, all
+//     products of one level stay below 2^23 in magnitude, so the FP32
+//     accumulation of tcgen05.mma is exact for each of the levels 2, 3, 4 and
+//     5, each in its own TMEM accumulator; levels 6..8 (below 2^(-32) of
+//     level 2) share a fifth, inexact one; levels above 8 (below 2^(-56)) are
+//     dropped;
+//   - the epilogue adds the five accumulators in FP64, exactly except for
+//     the last add, and updates M with one FMA by 2^(E_i + E_j): an update
+//     with FP64 rounding, at tensor-core speed.
+// The output tile is 128 columns j (TMEM lanes, so the FP64 read-modify-write
+// of row-major M is coalesced) x 64 rows i; TMA stages the 7 + 7 slices of a
+// tile (168 KiB, SWIZZLE_128B, no multicast), one thread issues the 28
+// MMAs x 4 K-steps.  Every wait is bounded as in the delayed flush.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "df.cuh"
+#include "internal.h"
+#include "tcgen05.cuh"
+
+namespace lru {
+
+constexpr int OZ_TJ = 128;                        // output columns j per tile (MMA M)
+constexpr int OZ_TI = 64;                         // output rows i per tile (MMA N)
+constexpr int OZ_SLICE_A = OZ_TJ * 128;           // bytes of one S slice tile (128 rows x 128 B)
+constexpr int OZ_SLICE_B = OZ_TI * 128;           // bytes of one Pan slice tile (64 rows x 128 B)
+constexpr int OZ_GROUPS = 5;                      // accumulators: levels 2, 3, 4, 5, 6..8
+constexpr uint32_t OZ_TMEM_COLS = 512;            // 5 x 64 columns, rounded to a power of two
+constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TI >> 3) << 17) |
+                              ((uint32_t)(OZ_TJ >> 4) << 24);   // BF16 x BF16 -> F32, K-major, 128 x 64
+
+struct OzMaps {
+    CUtensorMap S, P;
+};
+
+// ---- exact splitting (integer operations only) --------------------------------
+
+__device__ __forceinline__ int oz_bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// X = round(x * 2^(56 - E)) for |x| < 2^E: |X| < 2^56.  Zero and subnormal x give 0.
+__device__ __forceinline__ long long oz_fixed(double x, int E) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    if (eb == 0) return 0;
+    const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+    const int sh = eb - 1075 + 56 - E;   // <= 3 because |x| < 2^E
+    long long X;
+    if (sh >= 0) X = m << sh;
+    else if (sh > -60) X = (m + (1ll << (-sh - 1))) >> (-sh);
+    else X = 0;
+    return (b >> 63) ? -X : X;
+}
+
+// digit t of X (signed, rounded): X = sum_t d_t 2^(48 - 8t); BF16 bits of d_t * 2^(-8(t+1))
+__device__ __forceinline__ void oz_digits(long long X, uint16_t (&h)[OZ_S]) {
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) {
+        const int sh = 48 - 8 * t;
+        const long long q = sh > 0 ? ((X + (1ll << (sh - 1))) >> sh) : X;
+        X -= q << sh;
+        // |q| <= 256: exact in FP32 via the 1.5 * 2^23 offset, exact in BF16 (8 significant bits)
+        const float f = (__int_as_float(0x4B400000 + (int)q) - 12582912.0f) * __int_as_float((127 - 8 * (t + 1)) << 23);
+        h[t] = (uint16_t)(__float_as_uint(f) >> 16);
+    }
+}
+
+// Rows of (Pan - E): row i of walker w, columns k0 .. k0+63 of M, minus 1 at
+// (k0 + c, c).  One warp per row; lane covers c = lane and lane + 32.
+__global__ void __launch_bounds__(256) k_oz_slice_P(int n, int k0, OzWork Z, const uint8_t* mask) {
+    const int w = blockIdx.y;
+    if (mask && !mask[w]) return;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const double* row = Z.M + (long long)w * n * n + (long long)i * n + k0;
+    double a = row[lane], b = row[lane + 32];
+    if (i == k0 + lane) a -= 1.0;
+    if (i == k0 + lane + 32) b -= 1.0;
+    const int mx = __reduce_max_sync(0xffffffffu, max(oz_bexp(a), oz_bexp(b)));
+    const int E = mx > 0 ? mx - 1022 : 0;
+    uint16_t ha[OZ_S], hb[OZ_S];
+    oz_digits(oz_fixed(a, E), ha);
+    oz_digits(oz_fixed(b, E), hb);
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) {
+        uint16_t* dst = Z.Pb + (((long long)w * OZ_S + t) * n + i) * OZ_B;
+        dst[lane] = ha[t];
+        dst[lane + 32] = hb[t];
+    }
+    if (lane == 0) Z.eP[(long long)w * n + i] = E;
+}
+
+// Columns of S = rows k0 .. k0+63 of M: a 64 x 64 block per CTA through shared
+// memory (stored transposed), then one warp per column j.
+__global__ void __launch_bounds__(256) k_oz_slice_S(int n, int k0, OzWork Z, const uint8_t* mask) {
+    __shared__ double sT[64][65];   // sT[j][c] = S[c][j0 + j]
+    const int w = blockIdx.y;
+    if (mask && !mask[w]) return;
+    const int j0 = blockIdx.x * 64;
+    const double* M = Z.M + (long long)w * n * n;
+    for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+        const int c = e >> 6, j = e & 63;
+        sT[j][c] = M[(long long)(k0 + c) * n + j0 + j];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int j = threadIdx.x >> 5; j < 64; j += 8) {
+        const double a = sT[j][lane], b = sT[j][lane + 32];
+        const int mx = __reduce_max_sync(0xffffffffu, max(oz_bexp(a), oz_bexp(b)));
+        const int E = mx > 0 ? mx - 1022 : 0;
+        uint16_t ha[OZ_S], hb[OZ_S];
+        oz_digits(oz_fixed(a, E), ha);
+        oz_digits(oz_fixed(b, E), hb);
+#pragma unroll
+        for (int t = 0; t < OZ_S; ++t) {
+            uint16_t* dst = Z.Sb + (((long long)w * OZ_S + t) * n + j0 + j) * OZ_B;
+            dst[lane] = ha[t];
+            dst[lane + 32] = hb[t];
+        }
+        if (lane == 0) Z.eS[(long long)w * n + j0 + j] = E;
+    }
+}
+
+__device__ __forceinline__ void oz_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(dtmem), "l"(a), "l"(b), "r"(OZ_IDESC), "r"(acc)
+        : "memory");
+}
+
+// 2^e as a double for |e| < 1000
+__device__ __forceinline__ double oz_pow2(int e) { return __hiloint2double((e + 1023) << 20, 0); }
+
+// Trailing update of panel k0 for every (walker, 128-column, 64-row) tile,
+// persistent over the tiles; columns of the panel itself are left alone.
+__global__ void __launch_bounds__(256, 1)
+    k_oz_gemm(const __grid_constant__ OzMaps maps, int W, int n, int k0, OzWork Z, const uint8_t* mask, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = sm;                               // OZ_S slices of S, 128 rows each
+    unsigned char* sB = sA + OZ_S * OZ_SLICE_A;           // OZ_S slices of Pan, 64 rows each
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(OZ_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const uint32_t mb_tma = smem_u32(&mbar[0]), mb_mma = smem_u32(&mbar[1]);
+    const uint32_t tx_bytes = (uint32_t)OZ_S * (OZ_SLICE_A + OZ_SLICE_B);
+    const int ntj = n / OZ_TJ, nti = n / OZ_TI;
+    const long long per_w = (long long)ntj * nti;
+    const long long total = (long long)W * per_w;
+    uint32_t phase = 0;
+    for (long long ti = blockIdx.x; ti < total; ti += gridDim.x) {
+        const int w = (int)(ti / per_w);
+        const int rem = (int)(ti % per_w);
+        if (mask && !mask[w]) continue;
+        const int j0 = (rem % ntj) * OZ_TJ, i0 = (rem / ntj) * OZ_TI;
+        if (tid == 0) {
+            mbar_expect_tx(mb_tma, tx_bytes);
+            const int ys = (int)((long long)w * OZ_S * n);
+            for (int t = 0; t < OZ_S; ++t) {
+                tma_load_2d(smem_u32(sA + t * OZ_SLICE_A), &maps.S, 0, ys + t * n + j0, mb_tma);
+                tma_load_2d(smem_u32(sB + t * OZ_SLICE_B), &maps.P, 0, ys + t * n + i0, mb_tma);
+            }
+            if (!mbar_wait(mb_tma, phase)) {
+                set_dev_error(err, DEV_ERR_TIMEOUT);
+                s_abort = 1;
+                mbar_wait(mb_tma, phase);   // let copies in flight land before leaving
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                uint32_t started = 0;   // bit g: accumulator g holds a partial sum
+                for (int t = 0; t < OZ_S; ++t)
+                    for (int u = 0; u + t <= 6; ++u) {
+                        const int g = min(t + u, 4);   // level t + u + 2: 2, 3, 4, 5, 6..8
+                        const uint64_t a = desc_sw128(smem_u32(sA + t * OZ_SLICE_A));
+                        const uint64_t b = desc_sw128(smem_u32(sB + u * OZ_SLICE_B));
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t adv = (uint64_t)(ks * 32) >> 4;   // 16 BF16 along K per MMA
+                            oz_mma(tmem + 64u * g, a + adv, b + adv, (started >> g) & 1u);
+                            started |= 1u << g;
+                        }
+                    }
+                mma_commit(mb_mma);
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (!mbar_wait(mb_mma, phase)) {
+            set_dev_error(err, DEV_ERR_TIMEOUT);
+            s_abort = 1;
+        }
+        __syncthreads();
+        if (s_abort) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        phase ^= 1u;
+        // ---- epilogue: warp q reads TMEM lanes 32 (q % 4) .. +31 (columns j),
+        //      and rows i0 + 32 (q / 4) .. +31 in two chunks of 16 ----
+        const int quad = warp & 3, half = warp >> 2;
+        const int j = j0 + 32 * quad + lane;
+        const bool keep = !(j >= k0 && j < k0 + OZ_B);
+        const int eSj = Z.eS[(long long)w * n + j];
+        double* Mw = Z.M + (long long)w * n * n;
+        const int* eP = Z.eP + (long long)w * n;
+        for (int ch = 0; ch < 2; ++ch) {
+            const int c0 = 32 * half + 16 * ch;
+            float acc[OZ_GROUPS][16];
+#pragma unroll
+            for (int g = 0; g < OZ_GROUPS; ++g)
+                tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + 64u * g + (uint32_t)c0, acc[g]);
+            double m[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) m[c] = keep ? Mw[(long long)(i0 + c0 + c) * n + j] : 0.0;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                // exact through level 5 (each sum fits the 53-bit significand), one rounding for 6..8
+                double d = f2d_int(acc[0][c]) + f2d_int(acc[1][c]);
+                d += f2d_int(acc[2][c]);
+                d += f2d_int(acc[3][c]);
+                d += f2d_int(acc[4][c]);
+                const double s = oz_pow2(eP[i0 + c0 + c] + eSj);
+                if (keep) Mw[(long long)(i0 + c0 + c) * n + j] = fma(s, d, m[c]);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---- host side ----------------------------------------------------------------
+
+size_t oz_work_bytes(int W, int n) {
+    const size_t Wn = (size_t)W * n;
+    size_t b = 0;
+    auto take = [&](size_t x) { b += (x + 255) / 256 * 256; };
+    take(Wn * sizeof(int));                        // perm
+    take((size_t)W * sizeof(double));              // logacc
+    take((size_t)W * sizeof(double));              // sgnacc
+    take((size_t)W * sizeof(int));                 // sing
+    take(Wn * OZ_S * OZ_B * sizeof(uint16_t));     // Sb
+    take(Wn * OZ_S * OZ_B * sizeof(uint16_t));     // Pb
+    take(Wn * sizeof(int));                        // eS
+    take(Wn * sizeof(int));                        // eP
+    return b;
+}
+
+void oz_work_carve(OzWork& Z, void* base, int W, int n) {
+    const size_t Wn = (size_t)W * n;
+    unsigned char* p = (unsigned char*)base;
+    auto take = [&](size_t x) { unsigned char* q = p; p += (x + 255) / 256 * 256; return q; };
+    Z.perm = (int*)take(Wn * sizeof(int));
+    Z.logacc = (double*)take((size_t)W * sizeof(double));
+    Z.sgnacc = (double*)take((size_t)W * sizeof(double));
+    Z.sing = (int*)take((size_t)W * sizeof(int));
+    Z.Sb = (uint16_t*)take(Wn * OZ_S * OZ_B * sizeof(uint16_t));
+    Z.Pb = (uint16_t*)take(Wn * OZ_S * OZ_B * sizeof(uint16_t));
+    Z.eS = (int*)take(Wn * sizeof(int));
+    Z.eP = (int*)take(Wn * sizeof(int));
+}
+
+// rows x 64 BF16 matrix, box 64 x box_rows, SWIZZLE_128B
+static bool oz_map(CUtensorMap* m, const void* base, long long rows, int box_rows) {
+    EncodeTiled enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)OZ_B, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)OZ_B * 2};
+    cuuint32_t box[2] = {(cuuint32_t)OZ_B, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The whole refresh of the selected walkers: M = A^T (Z.M is the state's
+// A^{-1} storage), n / 64 panels, then the column permutation and log|det|.
+// Needs n % 128 == 0, 128 <= n <= 2048 and W <= 65535 (checked by the caller).
+bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const DevState<double>& S,
+                       const uint8_t* mask, bool delayed, int* err, cudaStream_t st) {
+    const long long rows = (long long)W * OZ_S * n;
+    if (rows >= (1ll << 31)) return false;
+    OzMaps maps;
+    if (!oz_map(&maps.S, Z.Sb, rows, OZ_TJ) || !oz_map(&maps.P, Z.Pb, rows, OZ_TI)) return false;
+    const size_t dyn = 1024 + (size_t)OZ_S * (OZ_SLICE_A + OZ_SLICE_B);
+    if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    launch_oz_load(W, n, A, Z.M, mask, st);
+    for (int k0 = 0; k0 < n; k0 += OZ_B) {
+        launch_oz_panel(W, n, k0, Z, mask, st);
+        k_oz_slice_P<<<dim3(n / 8, W), 256, 0, st>>>(n, k0, Z, mask);
+        k_oz_slice_S<<<dim3(n / 64, W), 256, 0, st>>>(n, k0, Z, mask);
+        k_oz_gemm<<<nsm, 256, dyn, st>>>(maps, W, n, k0, Z, mask, err);
+    }
+    launch_oz_finish(W, n, Z, S, mask, delayed, st);
+    return true;
+}
+
+}  // namespace lru

@@ -31,6 +31,7 @@ F64, C128, F32, C64 = 0, 1, 2, 3
 DET, PF = 0, 1
 FLUSH_NATIVE, FLUSH_TF32X3, FLUSH_TF32, FLUSH_BF16, FLUSH_BF16X3, FLUSH_DF = 0, 1, 2, 3, 4, 5
 ARITH_NATIVE, ARITH_DF = 0, 1
+REFRESH_AUTO, REFRESH_FP64, REFRESH_TENSOR = 0, 1, 2
 WALKER_OK, WALKER_SINGULAR, WALKER_NONFINITE, WALKER_BAD_INDEX = 0, 1, 2, 3
 
 _DTYPES = {torch.float64: F64, torch.complex128: C128, torch.float32: F32, torch.complex64: C64}
@@ -51,7 +52,8 @@ class _Config(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("walkers", C.c_int64), ("n", C.c_int32),
                 ("n_per_walker", C.POINTER(C.c_int32)), ("k", C.c_int32),
                 ("k_per_walker", C.POINTER(C.c_int32)), ("delay", C.c_int32), ("flush", C.c_int32),
-                ("device", C.c_int32), ("arith", C.c_int32), ("tile_chunks", C.c_int32)]
+                ("device", C.c_int32), ("arith", C.c_int32), ("tile_chunks", C.c_int32),
+                ("refresh", C.c_int32)]
 
 
 class _Operand(C.Structure):
@@ -170,7 +172,7 @@ class LowRankState:
 
     def __init__(self, kind: str, walkers: int, n, k: int = 1, dtype=torch.float64, delay: int = 0,
                  flush: int = FLUSH_NATIVE, k_per_walker=None, device: Optional[int] = None,
-                 arith: int = ARITH_NATIVE, tile_chunks: int = 0):
+                 arith: int = ARITH_NATIVE, tile_chunks: int = 0, refresh: int = 0):
         self.kind = {"det": DET, "pf": PF}[kind]
         self.dtype = dtype
         self.W = int(walkers)
@@ -202,6 +204,7 @@ class LowRankState:
         cfg.device = dev
         cfg.arith = int(arith)
         cfg.tile_chunks = int(tile_chunks)
+        cfg.refresh = int(refresh)
         h = _H()
         _check(_lib.lru_create(C.byref(cfg), C.byref(h)), "lru_create")
         self._h = h

@@ -60,12 +60,14 @@ class Cfg(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("walkers", ctypes.c_int64),
                 ("n", ctypes.c_int32), ("n_per_walker", ctypes.c_void_p), ("k", ctypes.c_int32),
                 ("k_per_walker", ctypes.c_void_p), ("delay", ctypes.c_int32), ("flush", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("arith", ctypes.c_int32), ("tile_chunks", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("arith", ctypes.c_int32), ("tile_chunks", ctypes.c_int32),
+                ("refresh", ctypes.c_int32)]
 
 
 @pytest.mark.parametrize("field,value,code", [
     ("kind", 7, 1), ("dtype", 9, 1), ("walkers", 0, 1), ("k", 0, 1), ("k", 17, 1),
     ("delay", -1, 1), ("flush", 11, 1), ("delay", 65, 1), ("arith", 3, 1), ("tile_chunks", -1, 1),
+    ("refresh", 3, 1), ("refresh", -1, 1), ("refresh", 2, 8),
 ])
 def test_create_rejects_bad_config_before_cuda(lib, field, value, code):
     cfg = Cfg(kind=0, dtype=0, walkers=4, n=16, n_per_walker=None, k=1, k_per_walker=None, delay=0,
