@@ -125,7 +125,7 @@ struct OzWork {
 size_t oz_work_bytes(int W, int n);
 void oz_work_carve(OzWork& Z, void* base, int W, int n);
 void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mask, cudaStream_t st);
-void launch_oz_panel(int W, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st);
+void launch_oz_panel(int W, int w0, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st);
 void launch_oz_finish(int W, int n, const OzWork& Z, const DevState<double>& S, const uint8_t* mask, bool delayed,
                       cudaStream_t st);
 bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const DevState<double>& S,

@@ -469,12 +469,12 @@ __global__ void k_oz_load(int n, const double* A, double* M, const uint8_t* mask
 // over all rows (updates confined to the panel), then its row exchanges
 // applied, in pivot order, to every column outside the panel.  log|pivot|
 // and the sign carry over between panels in Z.logacc / Z.sgnacc / Z.sing.
-__global__ void __launch_bounds__(RT) k_oz_panel(int n, int k0, OzWork Z, const uint8_t* mask) {
+__global__ void __launch_bounds__(RT) k_oz_panel(int n, int k0, int w0, OzWork Z, const uint8_t* mask) {
     extern __shared__ __align__(16) unsigned char dsm[];
     GJSmem<double>& sm = *reinterpret_cast<GJSmem<double>*>(dsm);
     __shared__ double s_log, s_sgn;
     __shared__ int s_sing;
-    const int w = blockIdx.x;
+    const int w = w0 + blockIdx.x;
     if (mask && !mask[w]) return;
     double* M = Z.M + (long long)w * n * n;
     int* perm = Z.perm + (long long)w * n;
@@ -548,10 +548,10 @@ void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mas
     k_oz_load<<<dim3(n / 32, n / 32, W), dim3(32, 8), 0, st>>>(n, A, M, mask);
 }
 
-void launch_oz_panel(int W, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st) {
+void launch_oz_panel(int W, int w0, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st) {
     const int dyn = (int)sizeof(GJSmem<double>);
     cudaFuncSetAttribute(k_oz_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-    k_oz_panel<<<W, RT, dyn, st>>>(n, k0, Z, mask);
+    k_oz_panel<<<W, RT, dyn, st>>>(n, k0, w0, Z, mask);
 }
 
 void launch_oz_finish(int W, int n, const OzWork& Z, const DevState<double>& S, const uint8_t* mask, bool delayed,

@@ -21,18 +21,21 @@
 //     5, each in its own TMEM accumulator; levels 6..8 (below 2^(-32) of
 //     level 2) share a fifth, inexact one; levels above 8 (below 2^(-56)) are
 //     dropped;
-//   - the epilogue adds the five accumulators in FP64, exactly except for
-//     the last add, and updates M with one FMA by 2^(E_i + E_j): an update
-//     with FP64 rounding, at tensor-core speed.
+//   - the epilogue recovers the four exact levels as integers, rounds the
+//     tail to a multiple of 2^-56, adds all five exactly in int64, converts
+//     once to double with the scale 2^(E_i + E_j) folded into the exponent
+//     (integer operations), and adds it to M: one FP64 add per element, and
+//     the rounding of an FP64 update, at tensor-core speed.
 // The output tile is 128 columns j (TMEM lanes, so the FP64 read-modify-write
-// of row-major M is coalesced) x 64 rows i; TMA stages the 7 + 7 slices of a
-// tile (168 KiB, SWIZZLE_128B, no multicast), one thread issues the 28
-// MMAs x 4 K-steps.  Every wait is bounded as in the delayed flush.
+// of row-major M is coalesced) x 64 rows i; TMA stages the 7 S slices of a
+// column block once (112 KiB) and the 7 Pan slices of each row tile (56 KiB)
+// behind the previous tile's epilogue (SWIZZLE_128B, no multicast); one
+// thread issues the 28 MMAs x 4 K-steps.  Every wait is bounded as in the
+// delayed flush.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
-#include "df.cuh"
 #include "internal.h"
 #include "tcgen05.cuh"
 
@@ -84,8 +87,8 @@ __device__ __forceinline__ void oz_digits(long long X, uint16_t (&h)[OZ_S]) {
 
 // Rows of (Pan - E): row i of walker w, columns k0 .. k0+63 of M, minus 1 at
 // (k0 + c, c).  One warp per row; lane covers c = lane and lane + 32.
-__global__ void __launch_bounds__(256) k_oz_slice_P(int n, int k0, OzWork Z, const uint8_t* mask) {
-    const int w = blockIdx.y;
+__global__ void __launch_bounds__(256) k_oz_slice_P(int n, int k0, int w0, OzWork Z, const uint8_t* mask) {
+    const int w = w0 + blockIdx.y;
     if (mask && !mask[w]) return;
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -110,9 +113,9 @@ __global__ void __launch_bounds__(256) k_oz_slice_P(int n, int k0, OzWork Z, con
 
 // Columns of S = rows k0 .. k0+63 of M: a 64 x 64 block per CTA through shared
 // memory (stored transposed), then one warp per column j.
-__global__ void __launch_bounds__(256) k_oz_slice_S(int n, int k0, OzWork Z, const uint8_t* mask) {
+__global__ void __launch_bounds__(256) k_oz_slice_S(int n, int k0, int w0, OzWork Z, const uint8_t* mask) {
     __shared__ double sT[64][65];   // sT[j][c] = S[c][j0 + j]
-    const int w = blockIdx.y;
+    const int w = w0 + blockIdx.y;
     if (mask && !mask[w]) return;
     const int j0 = blockIdx.x * 64;
     const double* M = Z.M + (long long)w * n * n;
@@ -147,13 +150,29 @@ __device__ __forceinline__ void oz_mma(uint32_t dtmem, uint64_t a, uint64_t b, u
         : "memory");
 }
 
-// 2^e as a double for |e| < 1000
-__device__ __forceinline__ double oz_pow2(int e) { return __hiloint2double((e + 1023) << 20, 0); }
+// F * 2^(e - 56) as a double, rounded to nearest even, by integer operations
+// (normal results only: the refresh's scales stay far from the exponent limits)
+__device__ __forceinline__ double oz_i64_to_double(long long F, int e) {
+    if (F == 0) return 0.0;
+    const unsigned long long sgn = (unsigned long long)F & 0x8000000000000000ull;
+    unsigned long long a = sgn ? (unsigned long long)(-F) : (unsigned long long)F;
+    const int lz = __clzll((long long)a);
+    a <<= lz;                                   // leading one at bit 63
+    unsigned long long mant = a >> 11;          // 53 bits
+    const unsigned r = (unsigned)(a & 0x7FFull);
+    mant += (r > 0x400u || (r == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+    int ex = 1023 + 63 - lz + e - 56;
+    if (mant >> 53) { mant >>= 1; ++ex; }
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
 
-// Trailing update of panel k0 for every (walker, 128-column, 64-row) tile,
-// persistent over the tiles; columns of the panel itself are left alone.
+// Trailing update of panel k0.  Persistent CTAs take (walker, 128-column
+// block) units: the 7 S slices of the block are loaded once, then the 64-row
+// tiles i stream through; the Pan slices of tile i+1 are loaded (TMA) while
+// the epilogue of tile i runs.  Columns of the panel itself are left alone.
 __global__ void __launch_bounds__(256, 1)
-    k_oz_gemm(const __grid_constant__ OzMaps maps, int W, int n, int k0, OzWork Z, const uint8_t* mask, int* err) {
+    k_oz_gemm(const __grid_constant__ OzMaps maps, int W, int w0, int n, int k0, OzWork Z, const uint8_t* mask,
+              int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -179,85 +198,104 @@ __global__ void __launch_bounds__(256, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
     const uint32_t mb_tma = smem_u32(&mbar[0]), mb_mma = smem_u32(&mbar[1]);
-    const uint32_t tx_bytes = (uint32_t)OZ_S * (OZ_SLICE_A + OZ_SLICE_B);
+    const uint32_t bytes_a = (uint32_t)OZ_S * OZ_SLICE_A, bytes_b = (uint32_t)OZ_S * OZ_SLICE_B;
     const int ntj = n / OZ_TJ, nti = n / OZ_TI;
-    const long long per_w = (long long)ntj * nti;
-    const long long total = (long long)W * per_w;
-    uint32_t phase = 0;
-    for (long long ti = blockIdx.x; ti < total; ti += gridDim.x) {
-        const int w = (int)(ti / per_w);
-        const int rem = (int)(ti % per_w);
+    const long long units = (long long)W * ntj;
+    uint32_t ph_tma = 0, ph_mma = 0;
+    for (long long un = blockIdx.x; un < units && !s_abort; un += gridDim.x) {
+        const int w = w0 + (int)(un / ntj);
         if (mask && !mask[w]) continue;
-        const int j0 = (rem % ntj) * OZ_TJ, i0 = (rem / ntj) * OZ_TI;
+        const int j0 = (int)(un % ntj) * OZ_TJ;
+        const int ys = (int)((long long)w * OZ_S * n);
         if (tid == 0) {
-            mbar_expect_tx(mb_tma, tx_bytes);
-            const int ys = (int)((long long)w * OZ_S * n);
+            mbar_expect_tx(mb_tma, bytes_a + bytes_b);
             for (int t = 0; t < OZ_S; ++t) {
                 tma_load_2d(smem_u32(sA + t * OZ_SLICE_A), &maps.S, 0, ys + t * n + j0, mb_tma);
-                tma_load_2d(smem_u32(sB + t * OZ_SLICE_B), &maps.P, 0, ys + t * n + i0, mb_tma);
-            }
-            if (!mbar_wait(mb_tma, phase)) {
-                set_dev_error(err, DEV_ERR_TIMEOUT);
-                s_abort = 1;
-                mbar_wait(mb_tma, phase);   // let copies in flight land before leaving
-            } else {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                uint32_t started = 0;   // bit g: accumulator g holds a partial sum
-                for (int t = 0; t < OZ_S; ++t)
-                    for (int u = 0; u + t <= 6; ++u) {
-                        const int g = min(t + u, 4);   // level t + u + 2: 2, 3, 4, 5, 6..8
-                        const uint64_t a = desc_sw128(smem_u32(sA + t * OZ_SLICE_A));
-                        const uint64_t b = desc_sw128(smem_u32(sB + u * OZ_SLICE_B));
-#pragma unroll
-                        for (int ks = 0; ks < 4; ++ks) {
-                            const uint64_t adv = (uint64_t)(ks * 32) >> 4;   // 16 BF16 along K per MMA
-                            oz_mma(tmem + 64u * g, a + adv, b + adv, (started >> g) & 1u);
-                            started |= 1u << g;
-                        }
-                    }
-                mma_commit(mb_mma);
+                tma_load_2d(smem_u32(sB + t * OZ_SLICE_B), &maps.P, 0, ys + t * n, mb_tma);
             }
         }
-        __syncthreads();
-        if (s_abort) break;
-        if (!mbar_wait(mb_mma, phase)) {
-            set_dev_error(err, DEV_ERR_TIMEOUT);
-            s_abort = 1;
-        }
-        __syncthreads();
-        if (s_abort) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        phase ^= 1u;
-        // ---- epilogue: warp q reads TMEM lanes 32 (q % 4) .. +31 (columns j),
-        //      and rows i0 + 32 (q / 4) .. +31 in two chunks of 16 ----
+        // per thread of the epilogue: column j (TMEM lane) and its scale
         const int quad = warp & 3, half = warp >> 2;
         const int j = j0 + 32 * quad + lane;
         const bool keep = !(j >= k0 && j < k0 + OZ_B);
         const int eSj = Z.eS[(long long)w * n + j];
         double* Mw = Z.M + (long long)w * n * n;
         const int* eP = Z.eP + (long long)w * n;
-        for (int ch = 0; ch < 2; ++ch) {
-            const int c0 = 32 * half + 16 * ch;
-            float acc[OZ_GROUPS][16];
+        for (int it = 0; it < nti; ++it) {
+            const int i0 = it * OZ_TI;
+            if (tid == 0) {
+                if (!mbar_wait(mb_tma, ph_tma)) {
+                    set_dev_error(err, DEV_ERR_TIMEOUT);
+                    s_abort = 1;
+                    mbar_wait(mb_tma, ph_tma);   // let copies in flight land before leaving
+                } else {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    uint32_t started = 0;   // bit g: accumulator g holds a partial sum
+                    for (int t = 0; t < OZ_S; ++t)
+                        for (int u = 0; u + t <= 6; ++u) {
+                            const int g = min(t + u, 4);   // level t + u + 2: 2, 3, 4, 5, 6..8
+                            const uint64_t a = desc_sw128(smem_u32(sA + t * OZ_SLICE_A));
+                            const uint64_t b = desc_sw128(smem_u32(sB + u * OZ_SLICE_B));
 #pragma unroll
-            for (int g = 0; g < OZ_GROUPS; ++g)
-                tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + 64u * g + (uint32_t)c0, acc[g]);
-            double m[16];
-#pragma unroll
-            for (int c = 0; c < 16; ++c) m[c] = keep ? Mw[(long long)(i0 + c0 + c) * n + j] : 0.0;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                // exact through level 5 (each sum fits the 53-bit significand), one rounding for 6..8
-                double d = f2d_int(acc[0][c]) + f2d_int(acc[1][c]);
-                d += f2d_int(acc[2][c]);
-                d += f2d_int(acc[3][c]);
-                d += f2d_int(acc[4][c]);
-                const double s = oz_pow2(eP[i0 + c0 + c] + eSj);
-                if (keep) Mw[(long long)(i0 + c0 + c) * n + j] = fma(s, d, m[c]);
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint64_t adv = (uint64_t)(ks * 32) >> 4;   // 16 BF16 along K per MMA
+                                oz_mma(tmem + 64u * g, a + adv, b + adv, (started >> g) & 1u);
+                                started |= 1u << g;
+                            }
+                        }
+                    mma_commit(mb_mma);
+                }
+                ph_tma ^= 1u;
             }
+            // this thread's 32 values of M (rows i0 + 32 (q / 4) ..): the loads
+            // overlap the MMAs
+            double m[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) m[c] = keep ? Mw[(long long)(i0 + 32 * half + c) * n + j] : 0.0;
+            __syncthreads();
+            if (s_abort) break;
+            if (!mbar_wait(mb_mma, ph_mma)) {
+                set_dev_error(err, DEV_ERR_TIMEOUT);
+                s_abort = 1;
+            }
+            ph_mma ^= 1u;
+            __syncthreads();
+            if (s_abort) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // the MMAs have read the Pan slices: load the next tile's during the epilogue
+            if (tid == 0 && it + 1 < nti) {
+                mbar_expect_tx(mb_tma, bytes_b);
+                for (int t = 0; t < OZ_S; ++t)
+                    tma_load_2d(smem_u32(sB + t * OZ_SLICE_B), &maps.P, 0, ys + t * n + i0 + OZ_TI, mb_tma);
+            }
+            // ---- epilogue: warp q reads TMEM lanes 32 (q % 4) .. +31 (columns j),
+            //      and rows i0 + 32 (q / 4) .. +31 in two chunks of 16 ----
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+                const int c0 = 32 * half + 16 * ch;
+                float acc[OZ_GROUPS][16];
+#pragma unroll
+                for (int g = 0; g < OZ_GROUPS; ++g)
+                    tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + 64u * g + (uint32_t)c0, acc[g]);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    // levels 2..5 are integers N_l 2^(-8l), |N_l| < 2^23, recovered exactly;
+                    // levels 6..8 rounded to a multiple of 2^-56.  F = sum in units of 2^-56
+                    // (|F| < 2^62): exact; one rounding to double, one in the add.
+                    const int n2 = __float2int_rn(acc[0][c] * 65536.0f);
+                    const int n3 = __float2int_rn(acc[1][c] * 16777216.0f);
+                    const int n4 = __float2int_rn(acc[2][c] * 4294967296.0f);
+                    const int n5 = __float2int_rn(acc[3][c] * 1099511627776.0f);
+                    const int tl = __float2int_rn(acc[4][c] * 72057594037927936.0f);
+                    const long long F =
+                        ((long long)(n2 * 256 + n3) << 32) + ((long long)(n4 * 256 + n5) << 16) + tl;
+                    const double d = oz_i64_to_double(F, eP[i0 + c0 + c] + eSj);
+                    if (keep) Mw[(long long)(i0 + c0 + c) * n + j] = m[16 * ch + c] + d;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
     }
     __syncthreads();
     if (warp == 0) {
@@ -329,10 +367,10 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     launch_oz_load(W, n, A, Z.M, mask, st);
     for (int k0 = 0; k0 < n; k0 += OZ_B) {
-        launch_oz_panel(W, n, k0, Z, mask, st);
-        k_oz_slice_P<<<dim3(n / 8, W), 256, 0, st>>>(n, k0, Z, mask);
-        k_oz_slice_S<<<dim3(n / 64, W), 256, 0, st>>>(n, k0, Z, mask);
-        k_oz_gemm<<<nsm, 256, dyn, st>>>(maps, W, n, k0, Z, mask, err);
+        launch_oz_panel(W, 0, n, k0, Z, mask, st);
+        k_oz_slice_P<<<dim3(n / 8, W), 256, 0, st>>>(n, k0, 0, Z, mask);
+        k_oz_slice_S<<<dim3(n / 64, W), 256, 0, st>>>(n, k0, 0, Z, mask);
+        k_oz_gemm<<<nsm, 256, dyn, st>>>(maps, W, 0, n, k0, Z, mask, err);
     }
     launch_oz_finish(W, n, Z, S, mask, delayed, st);
     return true;
