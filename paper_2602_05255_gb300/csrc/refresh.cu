@@ -504,6 +504,217 @@ __global__ void __launch_bounds__(RT) k_oz_panel(int n, int k0, int w0, OzWork Z
     }
 }
 
+// The same panel step with the rows in registers (n <= 1024): thread t owns
+// rows t + q * blockDim (q < RPT, blockDim = n / RPT).  Each 16-column
+// sub-panel is eliminated in registers (pivot by a block reduction, row
+// swaps through shared memory); its transform then updates the other 48
+// panel columns, M[r][j] = M[pi(r)][j] + sum_c (T - E)[r][c] S[c][j], with
+// the sub-panel's row exchanges folded in as the gather pi and the 16 pivot
+// rows S staged in shared memory.
+template <int RPT>
+__global__ void __launch_bounds__(512, 1) k_oz_panel_rows(int n, int k0, int w0, OzWork Z, const uint8_t* mask) {
+    constexpr int SW = 16;                   // sub-panel width
+    constexpr int NO = OZ_B - SW;            // other panel columns per sub-panel
+    __shared__ double s_S[SW][NO + 1];
+    __shared__ double s_rowk[SW], s_bufA[SW], s_bufB[SW];
+    __shared__ int s_pi[1024];
+    __shared__ double s_wv[16];
+    __shared__ int s_wi[16];
+    __shared__ double s_bv, s_log, s_sgn;
+    __shared__ int s_bi, s_sing;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    const int w = w0 + blockIdx.x;
+    if (mask && !mask[w]) return;
+    double* M = Z.M + (long long)w * n * n;
+    int* perm = Z.perm + (long long)w * n;
+    if (tid == 0) {
+        s_log = k0 ? Z.logacc[w] : 0.0;
+        s_sgn = k0 ? Z.sgnacc[w] : 1.0;
+        s_sing = k0 ? Z.sing[w] : 0;
+    }
+    __syncthreads();
+    for (int sp = 0; sp < OZ_B / SW; ++sp) {
+        const int ks = k0 + SW * sp;
+        double v[RPT][SW];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const double2* src = reinterpret_cast<const double2*>(M + (long long)(tid + q * nt) * n + ks);
+#pragma unroll
+            for (int c = 0; c < SW / 2; ++c) {
+                const double2 x = src[c];
+                v[q][2 * c] = x.x;
+                v[q][2 * c + 1] = x.y;
+            }
+        }
+#pragma unroll
+        for (int kc = 0; kc < SW; ++kc) {
+            const int k = ks + kc;
+            // ---- pivot: largest |v| over rows >= k (ties: smallest row) ----
+            double bv = -1.0;
+            int bi = -1;
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int r = tid + q * nt;
+                const double a = fabs(v[q][kc]);
+                if (r >= k && a > bv) { bv = a; bi = r; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) { bv = ov; bi = oi; }
+            }
+            if (lane == 0) { s_wv[wid] = bv; s_wi[wid] = bi; }
+            __syncthreads();
+            if (wid == 0) {
+                bv = lane < nt / 32 ? s_wv[lane] : -1.0;
+                bi = lane < nt / 32 ? s_wi[lane] : -1;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) { bv = ov; bi = oi; }
+                }
+                if (lane == 0) { s_bv = bv; s_bi = bi; }
+            }
+            __syncthreads();
+            const int p = s_bi;
+            if (!(s_bv > 0.0) || p < 0) {
+                if (tid == 0) { perm[k] = k; s_sing = 1; }
+                continue;
+            }
+            if (tid == 0) perm[k] = p;
+            const int tk = k % nt, qk = k / nt, tp = p % nt, qp = p / nt;
+            // ---- exchange rows k and p (sub-panel part) ----
+            if (p != k) {
+#pragma unroll
+                for (int q = 0; q < RPT; ++q) {
+                    if (tid == tk && q == qk)
+#pragma unroll
+                        for (int c = 0; c < SW; ++c) s_bufA[c] = v[q][c];
+                    if (tid == tp && q == qp)
+#pragma unroll
+                        for (int c = 0; c < SW; ++c) s_bufB[c] = v[q][c];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < RPT; ++q) {
+                    if (tid == tk && q == qk)
+#pragma unroll
+                        for (int c = 0; c < SW; ++c) v[q][c] = s_bufB[c];
+                    if (tid == tp && q == qp)
+#pragma unroll
+                        for (int c = 0; c < SW; ++c) v[q][c] = s_bufA[c];
+                }
+            }
+            // ---- scale the pivot row ----
+#pragma unroll
+            for (int q = 0; q < RPT; ++q)
+                if (tid == tk && q == qk) {
+                    const double piv = v[q][kc];
+                    const double ip = 1.0 / piv;
+#pragma unroll
+                    for (int c = 0; c < SW; ++c) {
+                        const double x = (c == kc ? 1.0 : v[q][c]) * ip;
+                        v[q][c] = x;
+                        s_rowk[c] = x;
+                    }
+                    s_log += log(fabs(piv));
+                    const double sg = piv < 0.0 ? -s_sgn : s_sgn;
+                    s_sgn = (p != k) ? -sg : sg;
+                }
+            __syncthreads();
+            // ---- eliminate column k from every other row ----
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int r = tid + q * nt;
+                if (r != k) {
+                    const double f = v[q][kc];
+#pragma unroll
+                    for (int c = 0; c < SW; ++c) v[q][c] = fma(-f, s_rowk[c], c == kc ? 0.0 : v[q][c]);
+                }
+            }
+        }
+        // ---- the sub-panel's transform columns back to M ----
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            double2* dst = reinterpret_cast<double2*>(M + (long long)(tid + q * nt) * n + ks);
+#pragma unroll
+            for (int c = 0; c < SW / 2; ++c) dst[c] = make_double2(v[q][2 * c], v[q][2 * c + 1]);
+        }
+        // ---- row gather of this sub-panel's exchanges, pivot rows S ----
+        for (int r = tid; r < n; r += nt) s_pi[r] = r;
+        __syncthreads();
+        if (tid == 0)
+            for (int kc = 0; kc < SW; ++kc) {
+                const int k = ks + kc, p = perm[k];
+                if (p != k) { const int t = s_pi[k]; s_pi[k] = s_pi[p]; s_pi[p] = t; }
+            }
+        __syncthreads();
+        for (int e = tid; e < SW * NO; e += nt) {
+            const int c = e / NO, jj = e % NO;
+            const int col = k0 + jj + (jj >= SW * sp ? SW : 0);
+            s_S[c][jj] = M[(long long)s_pi[ks + c] * n + col];
+        }
+        // (T - E): the identity comes off the pivot rows' own columns
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int r = tid + q * nt;
+#pragma unroll
+            for (int c = 0; c < SW; ++c)
+                if (r == ks + c) v[q][c] -= 1.0;
+        }
+        __syncthreads();
+        // ---- update of the other panel columns, CW at a time ----
+        constexpr int CW = RPT == 1 ? 8 : 4;
+        for (int ch = 0; ch < NO / CW; ++ch) {
+            const int jj0 = CW * ch;
+            const int col0 = k0 + jj0 + (jj0 >= SW * sp ? SW : 0);
+            double o[RPT][CW];
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const double2* src =
+                    reinterpret_cast<const double2*>(M + (long long)s_pi[tid + q * nt] * n + col0);
+#pragma unroll
+                for (int x = 0; x < CW / 2; ++x) {
+                    const double2 y = src[x];
+                    o[q][2 * x] = y.x;
+                    o[q][2 * x + 1] = y.y;
+                }
+            }
+            __syncthreads();   // every old row is read before any row is written
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+#pragma unroll
+                for (int c = 0; c < SW; ++c)
+#pragma unroll
+                    for (int x = 0; x < CW; ++x) o[q][x] = fma(v[q][c], s_S[c][jj0 + x], o[q][x]);
+                double2* dst = reinterpret_cast<double2*>(M + (long long)(tid + q * nt) * n + col0);
+#pragma unroll
+                for (int x = 0; x < CW / 2; ++x) dst[x] = make_double2(o[q][2 * x], o[q][2 * x + 1]);
+            }
+        }
+        __syncthreads();
+    }
+    // ---- the panel's exchanges on the columns outside it, in pivot order ----
+    for (int j = tid; j < n; j += nt) {
+        if (j >= k0 && j < k0 + OZ_B) continue;
+        for (int kc = 0; kc < OZ_B; ++kc) {
+            const int k = k0 + kc, p = perm[k];
+            if (p != k) {
+                const double a = M[(long long)k * n + j];
+                M[(long long)k * n + j] = M[(long long)p * n + j];
+                M[(long long)p * n + j] = a;
+            }
+        }
+    }
+    if (tid == 0) {
+        Z.logacc[w] = s_log;
+        Z.sgnacc[w] = s_sgn;
+        Z.sing[w] = s_sing;
+    }
+}
+
 // Undo the row exchanges of the elimination as one column permutation of
 // the inverse (idx composes the swaps, last first: M'[i][c] = M[i][idx[c]]),
 // four rows at a time through shared memory; then log|det|, sign and the
@@ -549,6 +760,14 @@ void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mas
 }
 
 void launch_oz_panel(int W, int w0, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st) {
+    if (n <= 512) {
+        k_oz_panel_rows<1><<<W, n, 0, st>>>(n, k0, w0, Z, mask);
+        return;
+    }
+    if (n <= 1024) {
+        k_oz_panel_rows<2><<<W, n / 2, 0, st>>>(n, k0, w0, Z, mask);
+        return;
+    }
     const int dyn = (int)sizeof(GJSmem<double>);
     cudaFuncSetAttribute(k_oz_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     k_oz_panel<<<W, RT, dyn, st>>>(n, k0, w0, Z, mask);
