@@ -170,7 +170,9 @@ __device__ __forceinline__ double oz_i64_to_double(long long F, int e) {
 // block) units: the 7 S slices of the block are loaded once, then the 64-row
 // tiles i stream through; the Pan slices of tile i+1 are loaded (TMA) while
 // the epilogue of tile i runs.  Columns of the panel itself are left alone.
-__global__ void __launch_bounds__(256, 1)
+constexpr int OZ_THREADS = 512;   // 16 warps: 4 per TMEM lane quarter, each 16 of the 64 rows i
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_gemm(const __grid_constant__ OzMaps maps, int W, int w0, int n, int k0, OzWork Z, const uint8_t* mask,
               int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(256, 1)
             }
         }
         // per thread of the epilogue: column j (TMEM lane) and its scale
-        const int quad = warp & 3, half = warp >> 2;
+        const int quad = warp & 3, part = warp >> 2;
         const int j = j0 + 32 * quad + lane;
         const bool keep = !(j >= k0 && j < k0 + OZ_B);
         const int eSj = Z.eS[(long long)w * n + j];
@@ -247,11 +249,11 @@ __global__ void __launch_bounds__(256, 1)
                 }
                 ph_tma ^= 1u;
             }
-            // this thread's 32 values of M (rows i0 + 32 (q / 4) ..): the loads
+            // this thread's 16 values of M (rows i0 + 16 (q / 4) ..): the loads
             // overlap the MMAs
-            double m[32];
+            double m[16];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) m[c] = keep ? Mw[(long long)(i0 + 32 * half + c) * n + j] : 0.0;
+            for (int c = 0; c < 16; ++c) m[c] = keep ? Mw[(long long)(i0 + 16 * part + c) * n + j] : 0.0;
             __syncthreads();
             if (s_abort) break;
             if (!mbar_wait(mb_mma, ph_mma)) {
@@ -269,16 +271,16 @@ __global__ void __launch_bounds__(256, 1)
                     tma_load_2d(smem_u32(sB + t * OZ_SLICE_B), &maps.P, 0, ys + t * n + i0 + OZ_TI, mb_tma);
             }
             // ---- epilogue: warp q reads TMEM lanes 32 (q % 4) .. +31 (columns j),
-            //      and rows i0 + 32 (q / 4) .. +31 in two chunks of 16 ----
+            //      and rows i0 + 16 (q / 4) .. +15 in two chunks of 8 ----
 #pragma unroll
             for (int ch = 0; ch < 2; ++ch) {
-                const int c0 = 32 * half + 16 * ch;
-                float acc[OZ_GROUPS][16];
+                const int c0 = 16 * part + 8 * ch;
+                float acc[OZ_GROUPS][8];
 #pragma unroll
                 for (int g = 0; g < OZ_GROUPS; ++g)
-                    tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + 64u * g + (uint32_t)c0, acc[g]);
+                    tmem_ld8(tmem + ((uint32_t)(32 * quad) << 16) + 64u * g + (uint32_t)c0, acc[g]);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
+                for (int c = 0; c < 8; ++c) {
                     // levels 2..5 are integers N_l 2^(-8l), |N_l| < 2^23, recovered exactly;
                     // levels 6..8 rounded to a multiple of 2^-56.  F = sum in units of 2^-56
                     // (|F| < 2^62): exact; one rounding to double, one in the add.
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(256, 1)
                     const long long F =
                         ((long long)(n2 * 256 + n3) << 32) + ((long long)(n4 * 256 + n5) << 16) + tl;
                     const double d = oz_i64_to_double(F, eP[i0 + c0 + c] + eSj);
-                    if (keep) Mw[(long long)(i0 + c0 + c) * n + j] = m[16 * ch + c] + d;
+                    if (keep) Mw[(long long)(i0 + c0 + c) * n + j] = m[8 * ch + c] + d;
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -370,7 +372,7 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
         launch_oz_panel(W, 0, n, k0, Z, mask, st);
         k_oz_slice_P<<<dim3(n / 8, W), 256, 0, st>>>(n, k0, 0, Z, mask);
         k_oz_slice_S<<<dim3(n / 64, W), 256, 0, st>>>(n, k0, 0, Z, mask);
-        k_oz_gemm<<<nsm, 256, dyn, st>>>(maps, W, 0, n, k0, Z, mask, err);
+        k_oz_gemm<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, k0, Z, mask, err);
     }
     launch_oz_finish(W, n, Z, S, mask, delayed, st);
     return true;
