@@ -317,7 +317,9 @@ lru_status lru_slogpf_batched(int32_t dtype, int64_t W, int32_t n, const void* A
 #define LRU_PROF_ACCEPT 1    /* the accept pass over A^{-1} (the Woodbury / GEMV pass) */
 #define LRU_PROF_FLUSH 2     /* the delayed flush contraction */
 #define LRU_PROF_REFRESH 3   /* from-scratch inverse (and Pfaffian) */
-#define LRU_PROF_CLASSES 4
+#define LRU_PROF_REFRESH_PANEL 4    /* within REFRESH (tensor-core form): the FP64 panel eliminations */
+#define LRU_PROF_REFRESH_UPDATE 5   /* within REFRESH (tensor-core form): the split-product trailing updates */
+#define LRU_PROF_CLASSES 6
 /* on != 0: record a CUDA event pair around every launch of each class. */
 lru_status lru_profile_enable(lru_handle h, int32_t on);
 /* Synchronises the stream; total_ms / launches (either may be NULL) receive

@@ -128,8 +128,10 @@ void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mas
 void launch_oz_panel(int W, int w0, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st);
 void launch_oz_finish(int W, int n, const OzWork& Z, const DevState<double>& S, const uint8_t* mask, bool delayed,
                       cudaStream_t st);
+// hook(ctx, class, begin) brackets the panel (class 4) and update (class 5) launches
 bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const DevState<double>& S,
-                       const uint8_t* mask, bool delayed, int* err, cudaStream_t st);
+                       const uint8_t* mask, bool delayed, int* err, cudaStream_t st,
+                       void (*hook)(void*, int, int), void* hctx);
 void launch_wait_selftest(const int* flag, long long iters, int* err, cudaStream_t st);
 void launch_commit_moves(int W, int n, int k, int* occ, const int* slot, const int* newrow, const uint8_t* mask,
                          const int* pst, cudaStream_t st);

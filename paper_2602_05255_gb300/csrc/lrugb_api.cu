@@ -77,8 +77,8 @@ struct lru_ctx {
     int nws = 0;
     // profiling: event pairs per kernel class, and a launch counter
     bool prof_on = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[4];
-    size_t prof_used[4] = {0, 0, 0, 0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[LRU_PROF_CLASSES];
+    size_t prof_used[LRU_PROF_CLASSES] = {};
     long long launches = 0;
     // last proposal
     bool has_prop = false;
@@ -428,6 +428,12 @@ lru_status lru_device_bytes(lru_handle h, size_t* bytes) {
     return LRU_OK;
 }
 
+static void oz_prof_hook(void* p, int cls, int begin) {
+    lru_ctx* h = (lru_ctx*)p;
+    if (begin) prof_begin(h, cls);
+    else prof_end(h, cls);
+}
+
 static lru_status ensure_oz(lru_ctx* h) {
     if (h->ozw) return LRU_OK;
     const size_t b = oz_work_bytes(h->W, h->n_uni);
@@ -454,7 +460,7 @@ static lru_status do_init(lru_handle h, const void* A, const uint8_t* mask, doub
         DevState<double> S = h->state<double>();
         prof_begin(h, LRU_PROF_REFRESH);
         const bool ok = launch_refresh_oz(h->W, h->n_uni, (const double*)A, Z, S, mask, h->delayed, h->err,
-                                          h->stream);
+                                          h->stream, h->prof_on ? oz_prof_hook : nullptr, h);
         prof_end(h, LRU_PROF_REFRESH);
         if (ok) {
             h->launches += 2 + 4 * (h->n_uni / OZ_B);

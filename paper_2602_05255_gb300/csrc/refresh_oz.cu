@@ -354,7 +354,8 @@ static bool oz_map(CUtensorMap* m, const void* base, long long rows, int box_row
 // A^{-1} storage), n / 64 panels, then the column permutation and log|det|.
 // Needs n % 128 == 0, 128 <= n <= 2048 and W <= 65535 (checked by the caller).
 bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const DevState<double>& S,
-                       const uint8_t* mask, bool delayed, int* err, cudaStream_t st) {
+                       const uint8_t* mask, bool delayed, int* err, cudaStream_t st,
+                       void (*hook)(void*, int, int), void* hctx) {
     const long long rows = (long long)W * OZ_S * n;
     if (rows >= (1ll << 31)) return false;
     OzMaps maps;
@@ -369,10 +370,13 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     launch_oz_load(W, n, A, Z.M, mask, st);
     for (int k0 = 0; k0 < n; k0 += OZ_B) {
+        if (hook) hook(hctx, 4, 1);
         launch_oz_panel(W, 0, n, k0, Z, mask, st);
+        if (hook) { hook(hctx, 4, 0); hook(hctx, 5, 1); }
         k_oz_slice_P<<<dim3(n / 8, W), 256, 0, st>>>(n, k0, 0, Z, mask);
         k_oz_slice_S<<<dim3(n / 64, W), 256, 0, st>>>(n, k0, 0, Z, mask);
         k_oz_gemm<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, k0, Z, mask, err);
+        if (hook) hook(hctx, 5, 0);
     }
     launch_oz_finish(W, n, Z, S, mask, delayed, st);
     return true;
