@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--m", type=int, default=2048)
     p.add_argument("--delay", type=int, default=16)
     p.add_argument("--refresh-every", type=int, default=128)
-    p.add_argument("--arms", default="plain,delayed,delayed_tf32x3,delayed_dfgemv",
+    p.add_argument("--arms", default="plain,delayed,delayed_dfflush,delayed_tf32x3,delayed_dfgemv",
                    help="comma list of " + ",".join(ARMS))
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -141,13 +141,14 @@ def cpu_baseline(Phi, occ0, slot, new, n, budget_s=15.0):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
-FLUSH = {"native": 0, "tf32x3": 1, "tf32": 2, "bf16": 3, "bf16x3": 4, "df": 5}
+FLUSH = {"native": 0, "tf32x3": 1, "tf32": 2, "bf16": 3, "bf16x3": 4, "df": 5, "split": 6}
 ARITH = {"native": 0, "df": 1}
 
 # name -> (delay, arith, flush); "delayed" is the headline form
 ARMS = {
     "plain": (0, "native", "native"),              # FP64 Sherman-Morrison step (Eq. det_inv)
-    "delayed": (None, "native", "df"),             # FP64 GEMV, double-float flush
+    "delayed": (None, "native", "split"),          # FP64 GEMV, exact split-product tensor-core flush
+    "delayed_dfflush": (None, "native", "df"),     # FP64 GEMV, double-float flush (FP32 pipe)
     "delayed_tf32x3": (None, "native", "tf32x3"),  # FP64 GEMV, tensor-core TF32x3 flush (precision form)
     "delayed_dfgemv": (None, "df", "df"),          # double-float GEMV and flush
 }

@@ -121,6 +121,7 @@ struct OzWork {
     uint16_t* Pb;     // W x OZ_S x n x OZ_B  BF16 slices of the rows of (panel - E)
     int* eS;          // W x n  power-of-two exponents of the S columns
     int* eP;          // W x n  power-of-two exponents of the panel rows
+    uint8_t* go;      // W      walkers that flush now (split-product flush)
 };
 size_t oz_work_bytes(int W, int n);
 void oz_work_carve(OzWork& Z, void* base, int W, int n);
@@ -128,6 +129,10 @@ void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mas
 void launch_oz_panel(int W, int w0, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st);
 void launch_oz_finish(int W, int n, const OzWork& Z, const DevState<double>& S, const uint8_t* mask, bool delayed,
                       cudaStream_t st);
+// delayed determinant flush A_0^{-1} -= P Q^T as the same exact split product
+// (uniform n, n % 128 == 0, Kc <= 64); walkers with tau >= K, or force && tau > 0
+bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, const double* Q, const int* tau,
+                        const uint8_t* force, const OzWork& Z, int* err, cudaStream_t st);
 // hook(ctx, class, begin) brackets the panel (class 4) and update (class 5) launches
 bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const DevState<double>& S,
                        const uint8_t* mask, bool delayed, int* err, cudaStream_t st,

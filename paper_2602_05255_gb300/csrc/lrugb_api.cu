@@ -211,7 +211,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     const int kk = cfg->kind == LRU_PF ? 2 * cfg->k : cfg->k;
     if (kk > MAXKK) return LRU_ERR_ARG;
     if (cfg->delay < 0) return LRU_ERR_ARG;
-    if (cfg->flush < LRU_FLUSH_NATIVE || cfg->flush > LRU_FLUSH_DF) return LRU_ERR_ARG;
+    if (cfg->flush < LRU_FLUSH_NATIVE || cfg->flush > LRU_FLUSH_SPLIT) return LRU_ERR_ARG;
     if (cfg->arith != LRU_ARITH_NATIVE && cfg->arith != LRU_ARITH_DF) return LRU_ERR_ARG;
     if (cfg->tile_chunks < 0) return LRU_ERR_ARG;
     if (cfg->refresh < LRU_REFRESH_AUTO || cfg->refresh > LRU_REFRESH_TENSOR) return LRU_ERR_ARG;
@@ -273,6 +273,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
                           h->W <= 65535;
         if (cfg->refresh == LRU_REFRESH_TENSOR && !fits) { delete h; return LRU_ERR_UNSUPPORTED; }
         h->oz_ok = fits && cfg->refresh != LRU_REFRESH_FP64;
+        if (cfg->flush == LRU_FLUSH_SPLIT && !(fits && delayed && h->Kc <= 64)) { delete h; return LRU_ERR_UNSUPPORTED; }
     }
 
     if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); delete h; return LRU_ERR_CUDA; }
@@ -314,7 +315,8 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     }
 
     // one allocation: persistent state first, then scratch and metadata
-    const bool tc = delayed && cfg->flush != LRU_FLUSH_NATIVE && cfg->flush != LRU_FLUSH_DF;
+    const bool tc = delayed && cfg->flush != LRU_FLUSH_NATIVE && cfg->flush != LRU_FLUSH_DF &&
+                    cfg->flush != LRU_FLUSH_SPLIT;
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b); return o; };
     const size_t oG = take((size_t)h->sum_n2 * sz);
@@ -609,7 +611,19 @@ static lru_status do_flush(lru_handle h, const uint8_t* force) {
     DevLayout L = h->layout();
     prof_begin(h, LRU_PROF_FLUSH);
     h->launches += 2;
-    if (h->flush == LRU_FLUSH_DF) {
+    if (h->flush == LRU_FLUSH_SPLIT) {
+        lru_status s = ensure_oz(h);
+        if (s != LRU_OK) { prof_end(h, LRU_PROF_FLUSH); return s; }
+        OzWork Z{};
+        oz_work_carve(Z, h->ozw, h->W, h->n_uni);
+        Z.M = (double*)h->G;
+        h->launches += 2;
+        if (!launch_flush_split(h->W, h->n_uni, h->K, h->Kc, h->kk, (const double*)h->P, (const double*)h->Q,
+                                h->tau, force, Z, h->err, h->stream)) {
+            prof_end(h, LRU_PROF_FLUSH);
+            return LRU_ERR_UNSUPPORTED;
+        }
+    } else if (h->flush == LRU_FLUSH_DF) {
         launch_flush_df(h->pf, L, h->state<double>(), force, h->stream);
     } else if (h->flush != LRU_FLUSH_NATIVE) {
         if (force) LRU_DISPATCH(h, { launch_zero_split_tail<T>(L, h->state<T>(), force, h->stream); });

@@ -17,12 +17,15 @@
 //   - the product of digit t of S and digit u of Pan has level l = t + u + 2:
 //     an integer times 2^(-8l).  Summed over the 64-wide inner dimension, all
 //     products of one level stay below 2^23 in magnitude, so the FP32
-//     accumulation of tcgen05.mma is exact for each of the levels 2, 3, 4 and
-//     5, each in its own TMEM accumulator; levels 6..8 (below 2^(-32) of
-//     level 2) share a fifth, inexact one; levels above 8 (below 2^(-56)) are
-//     dropped;
-//   - the epilogue recovers the four exact levels as integers, rounds the
-//     tail to a multiple of 2^-56, adds all five exactly in int64, converts
+//     accumulation of tcgen05.mma is exact for each of the levels 2 .. 6,
+//     each in its own TMEM accumulator; levels 7..10 (below 2^(-40) of level
+//     2, summed with FP32 rounding) share a sixth; levels above 10 (below
+//     2^(-66) of the scale) are dropped.  Levels 7..10 are kept because the
+//     row scaling measures errors against the row maxima: a level dropped at
+//     2^-56 of the maxima of two rows whose large entries do not meet costs
+//     far more than 2^-53 of the products actually summed;
+//   - the epilogue recovers the five exact levels as integers, rounds the
+//     tail to a multiple of 2^-56, adds all six exactly in int64, converts
 //     once to double with the scale 2^(E_i + E_j) folded into the exponent
 //     (integer operations), and adds it to M: one FP64 add per element, and
 //     the rounding of an FP64 update, at tensor-core speed.
@@ -30,8 +33,10 @@
 // of row-major M is coalesced) x 64 rows i; TMA stages the 7 S slices of a
 // column block once (112 KiB) and the 7 Pan slices of each row tile (56 KiB)
 // behind the previous tile's epilogue (SWIZZLE_128B, no multicast); one
-// thread issues the 28 MMAs x 4 K-steps.  Every wait is bounded as in the
-// delayed flush.
+// thread issues the 39 MMAs x 4 K-steps.  Every wait is bounded as in the
+// delayed flush.  (Two accumulator sets for an MMA / epilogue overlap do not
+// fit the 512 TMEM columns at 64 rows; at 32 rows the MMAs, whose operands
+// are re-read from shared memory per instruction, become the bound.)
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -45,8 +50,9 @@ constexpr int OZ_TJ = 128;                        // output columns j per tile (
 constexpr int OZ_TI = 64;                         // output rows i per tile (MMA N)
 constexpr int OZ_SLICE_A = OZ_TJ * 128;           // bytes of one S slice tile (128 rows x 128 B)
 constexpr int OZ_SLICE_B = OZ_TI * 128;           // bytes of one Pan slice tile (64 rows x 128 B)
-constexpr int OZ_GROUPS = 5;                      // accumulators: levels 2, 3, 4, 5, 6..8
-constexpr uint32_t OZ_TMEM_COLS = 512;            // 5 x 64 columns, rounded to a power of two
+constexpr int OZ_GROUPS = 6;                      // accumulators: levels 2, 3, 4, 5, 6 (exact), 7..10
+constexpr int OZ_MAXLV = 8;                       // products t + u <= 8 (levels up to 10) are kept
+constexpr uint32_t OZ_TMEM_COLS = 512;            // 6 x 64 columns, rounded to a power of two
 constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TI >> 3) << 17) |
                               ((uint32_t)(OZ_TJ >> 4) << 24);   // BF16 x BF16 -> F32, K-major, 128 x 64
 
@@ -166,15 +172,16 @@ __device__ __forceinline__ double oz_i64_to_double(long long F, int e) {
     return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
-// Trailing update of panel k0.  Persistent CTAs take (walker, 128-column
+// Trailing update of panel k0 (nks K-steps of 16: 4 for a 64-column panel).
+// Persistent CTAs take (walker, 128-column
 // block) units: the 7 S slices of the block are loaded once, then the 64-row
 // tiles i stream through; the Pan slices of tile i+1 are loaded (TMA) while
 // the epilogue of tile i runs.  Columns of the panel itself are left alone.
 constexpr int OZ_THREADS = 512;   // 16 warps: 4 per TMEM lane quarter, each 16 of the 64 rows i
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_oz_gemm(const __grid_constant__ OzMaps maps, int W, int w0, int n, int k0, OzWork Z, const uint8_t* mask,
-              int* err) {
+    k_oz_gemm(const __grid_constant__ OzMaps maps, int W, int w0, int n, int k0, int nks, OzWork Z,
+              const uint8_t* mask, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -234,12 +241,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     uint32_t started = 0;   // bit g: accumulator g holds a partial sum
                     for (int t = 0; t < OZ_S; ++t)
-                        for (int u = 0; u + t <= 6; ++u) {
-                            const int g = min(t + u, 4);   // level t + u + 2: 2, 3, 4, 5, 6..8
+                        for (int u = 0; u < OZ_S && u + t <= OZ_MAXLV; ++u) {
+                            const int g = min(t + u, OZ_GROUPS - 1);   // level t+u+2: 2 .. 6, then 7..10
                             const uint64_t a = desc_sw128(smem_u32(sA + t * OZ_SLICE_A));
                             const uint64_t b = desc_sw128(smem_u32(sB + u * OZ_SLICE_B));
-#pragma unroll
-                            for (int ks = 0; ks < 4; ++ks) {
+                            for (int ks = 0; ks < nks; ++ks) {
                                 const uint64_t adv = (uint64_t)(ks * 32) >> 4;   // 16 BF16 along K per MMA
                                 oz_mma(tmem + 64u * g, a + adv, b + adv, (started >> g) & 1u);
                                 started |= 1u << g;
@@ -281,16 +287,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     tmem_ld8(tmem + ((uint32_t)(32 * quad) << 16) + 64u * g + (uint32_t)c0, acc[g]);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    // levels 2..5 are integers N_l 2^(-8l), |N_l| < 2^23, recovered exactly;
-                    // levels 6..8 rounded to a multiple of 2^-56.  F = sum in units of 2^-56
+                    // levels 2..6 are integers N_l 2^(-8l), |N_l| < 2^23, recovered exactly;
+                    // levels 7..10 rounded to a multiple of 2^-56.  F = sum in units of 2^-56
                     // (|F| < 2^62): exact; one rounding to double, one in the add.
                     const int n2 = __float2int_rn(acc[0][c] * 65536.0f);
                     const int n3 = __float2int_rn(acc[1][c] * 16777216.0f);
                     const int n4 = __float2int_rn(acc[2][c] * 4294967296.0f);
                     const int n5 = __float2int_rn(acc[3][c] * 1099511627776.0f);
-                    const int tl = __float2int_rn(acc[4][c] * 72057594037927936.0f);
-                    const long long F =
-                        ((long long)(n2 * 256 + n3) << 32) + ((long long)(n4 * 256 + n5) << 16) + tl;
+                    const int n6 = __float2int_rn(acc[4][c] * 281474976710656.0f);
+                    const int tl = __float2int_rn(acc[5][c] * 72057594037927936.0f);
+                    const long long F = ((long long)(n2 * 256 + n3) << 32) + ((long long)(n4 * 256 + n5) << 16) +
+                                        ((long long)n6 << 8) + tl;
                     const double d = oz_i64_to_double(F, eP[i0 + c0 + c] + eSj);
                     if (keep) Mw[(long long)(i0 + c0 + c) * n + j] = m[8 * ch + c] + d;
                 }
@@ -304,6 +311,43 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS)
                      : "memory");
     }
+}
+
+// ---- the delayed flush as a split product ------------------------------------
+
+__global__ void k_oz_flush_go(int W, int K, const int* tau, const uint8_t* force, uint8_t* go) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    const int t = tau[w];
+    go[w] = (force ? (force[w] && t > 0) : (t >= K)) ? 1 : 0;
+}
+
+// Row r of walker w's slot matrix X (rows of ldx doubles): the cu = tau * kk
+// filled slot columns times sgn, zeros after; one warp per row, slices and
+// exponent as for the panel rows.
+__global__ void __launch_bounds__(256) k_oz_slice_rows(int n, int ldx, int kk, const double* X, double sgn,
+                                                       const int* tau, const uint8_t* go, uint16_t* dst, int* ex) {
+    const int w = blockIdx.y;
+    if (!go[w]) return;
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= n) return;
+    const int cu = tau[w] * kk;
+    const double* row = X + ((long long)w * n + r) * ldx;
+    const double a = lane < cu ? sgn * row[lane] : 0.0;
+    const double b = lane + 32 < cu ? sgn * row[lane + 32] : 0.0;
+    const int mx = __reduce_max_sync(0xffffffffu, max(oz_bexp(a), oz_bexp(b)));
+    const int E = mx > 0 ? mx - 1022 : 0;
+    uint16_t ha[OZ_S], hb[OZ_S];
+    oz_digits(oz_fixed(a, E), ha);
+    oz_digits(oz_fixed(b, E), hb);
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) {
+        uint16_t* d = dst + (((long long)w * OZ_S + t) * n + r) * OZ_B;
+        d[lane] = ha[t];
+        d[lane + 32] = hb[t];
+    }
+    if (lane == 0) ex[(long long)w * n + r] = E;
 }
 
 // ---- host side ----------------------------------------------------------------
@@ -320,6 +364,7 @@ size_t oz_work_bytes(int W, int n) {
     take(Wn * OZ_S * OZ_B * sizeof(uint16_t));     // Pb
     take(Wn * sizeof(int));                        // eS
     take(Wn * sizeof(int));                        // eP
+    take((size_t)W);                               // go
     return b;
 }
 
@@ -335,6 +380,7 @@ void oz_work_carve(OzWork& Z, void* base, int W, int n) {
     Z.Pb = (uint16_t*)take(Wn * OZ_S * OZ_B * sizeof(uint16_t));
     Z.eS = (int*)take(Wn * sizeof(int));
     Z.eP = (int*)take(Wn * sizeof(int));
+    Z.go = (uint8_t*)take((size_t)W);
 }
 
 // rows x 64 BF16 matrix, box 64 x box_rows, SWIZZLE_128B
@@ -375,10 +421,47 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
         if (hook) { hook(hctx, 4, 0); hook(hctx, 5, 1); }
         k_oz_slice_P<<<dim3(n / 8, W), 256, 0, st>>>(n, k0, 0, Z, mask);
         k_oz_slice_S<<<dim3(n / 64, W), 256, 0, st>>>(n, k0, 0, Z, mask);
-        k_oz_gemm<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, k0, Z, mask, err);
+        k_oz_gemm<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, k0, OZ_B / 16, Z, mask, err);
         if (hook) hook(hctx, 5, 0);
     }
     launch_oz_finish(W, n, Z, S, mask, delayed, st);
+    return true;
+}
+
+// A_0^{-1} -= P Q^T (Sec. 2.3, Eq. delayed_Ainv) for the walkers that flush:
+// with M = the stored A_0^{-1} (row l of storage = column l of A_0^{-1}),
+// M[l][j] += sum_c (-Q)[l][c] P[j][c]: the P rows take the place of the S
+// columns, the -Q rows that of the panel rows, no column is skipped.
+bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, const double* Q, const int* tau,
+                        const uint8_t* force, const OzWork& Z, int* err, cudaStream_t st) {
+    if (Kc < 1 || Kc > OZ_B) return false;
+    const long long rows = (long long)W * OZ_S * n;
+    if (rows >= (1ll << 31)) return false;
+    static thread_local OzMaps maps;
+    static thread_local const void* cached[2] = {nullptr, nullptr};
+    static thread_local long long cached_rows = -1;
+    if (cached[0] != Z.Sb || cached[1] != Z.Pb || cached_rows != rows) {
+        if (!oz_map(&maps.S, Z.Sb, rows, OZ_TJ) || !oz_map(&maps.P, Z.Pb, rows, OZ_TI)) return false;
+        cached[0] = Z.Sb;
+        cached[1] = Z.Pb;
+        cached_rows = rows;
+    }
+    const size_t dyn = 1024 + (size_t)OZ_S * (OZ_SLICE_A + OZ_SLICE_B);
+    static thread_local bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        attr = true;
+    }
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    k_oz_flush_go<<<(W + 255) / 256, 256, 0, st>>>(W, K, tau, force, Z.go);
+    k_oz_slice_rows<<<dim3(n / 8, W), 256, 0, st>>>(n, Kc, kk, P, 1.0, tau, Z.go, Z.Sb, Z.eS);
+    k_oz_slice_rows<<<dim3(n / 8, W), 256, 0, st>>>(n, Kc, kk, Q, -1.0, tau, Z.go, Z.Pb, Z.eP);
+    k_oz_gemm<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, n, (Kc + 15) / 16, Z, Z.go, err);
     return true;
 }
 

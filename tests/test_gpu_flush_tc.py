@@ -204,3 +204,96 @@ def test_forced_partial_flush(flush):
         if not mask[w]:
             assert np.array_equal(after[w], before[w])
     st.check_device_error()
+
+
+# ---- exact split-product flush on the tensor cores (FP64 bar) -------------------
+
+def test_split_flush_precision_well_conditioned():
+    L = lrugb()
+    st, worst, inv_err = well_conditioned_chain(L, 5, 256, 16, 40, L.FLUSH_SPLIT, L.ARITH_NATIVE, 611)
+    assert worst <= 1e-12 and inv_err <= 1e-12, (worst, inv_err)
+    st.check_device_error()
+
+
+@pytest.mark.parametrize("K", [8, 16])
+def test_split_flush_on_slater_chain(K):
+    # realistic Slater chain at the FP64 bar (plain FP64 rounding scale)
+    L = lrugb()
+    W, n, steps = 4, 256, 40
+    Phi, occ0, slot, new = det_workload(720 + K, W, n, 2 * n, steps)
+    st, ratios, status, _ = run_det_chain_gpu(L, Phi, occ0, slot, new, delay=K, flush=L.FLUSH_SPLIT)
+    assert (status == 0).all()
+    inv = st.inverse().cpu().numpy()
+    for w in range(W):
+        rs, inv_ref, occ, ex = replay_det_oracle(Phi, occ0, slot, new, w, delay=K)
+        check_ratios(ratios[:, w], rs, ex, what=w)
+        # A^{-1} against the exact inverse, with the oracle chain's own FP64 drift as the scale
+        exact = O.inv(O.slater_matrix(Phi, occ))
+        assert fro_rel(inv[w], exact) <= max(1e-10, 10 * fro_rel(inv_ref, exact))
+    st.check_device_error()
+
+
+def test_split_flush_forced_partial():
+    L = lrugb()
+    W, n, K, steps = 4, 128, 8, 23        # 2 full windows, then 7 pending
+    st, _, _ = well_conditioned_chain(L, W, n, K, steps, L.FLUSH_SPLIT, L.ARITH_NATIVE, 631)
+    before = st.inverse().cpu().numpy()
+    mask = np.array([1, 0, 1, 1], np.uint8)
+    st.flush(tdev(mask))
+    tau = st.tau().cpu().numpy()
+    after = st.inverse().cpu().numpy()
+    for w in range(W):
+        assert fro_rel(after[w], before[w]) <= 1e-12
+        assert tau[w] == (0 if mask[w] else steps % K)
+        if not mask[w]:
+            assert np.array_equal(after[w], before[w])
+    st.check_device_error()
+
+
+def test_split_flush_rejects_unsupported_shapes():
+    L = lrugb()
+    with pytest.raises(L.LRUError):   # n not a multiple of 128
+        L.LowRankState("det", 2, 200, k=1, dtype=torch.float64, delay=8, flush=L.FLUSH_SPLIT)
+    with pytest.raises(L.LRUError):   # Pfaffian
+        L.LowRankState("pf", 2, 256, k=1, dtype=torch.float64, delay=8, flush=L.FLUSH_SPLIT)
+
+
+def test_split_flush_against_exact_rational_arithmetic():
+    # A_0^{-1} -= P Q^T on planted slots with a wide dynamic range across slot
+    # columns, against exact rational arithmetic.  The split product's error
+    # bound is relative to the row maxima: |err| <= 2^-52 (maxP_j sum|Q_l| +
+    # sum|P_j| maxQ_l) + 2^-52 |result| (quantisation to 2^-56 of the maxima,
+    # levels kept down to 2^-66, two FP64 roundings).
+    from fractions import Fraction
+    L = lrugb()
+    W, n, K = 2, 128, 16
+    st = L.LowRankState("det", W, n, k=1, dtype=torch.float64, delay=K, flush=L.FLUSH_SPLIT)
+    g = np.random.Generator(np.random.PCG64(641))
+    st.init(tdev(g.standard_normal((W, n, n)) + 4 * np.eye(n)))
+    buf = st.save().cpu().numpy().copy()
+    al = lambda x: (x + 255) // 256 * 256
+    oG, oP = 0, al(W * n * n * 8)
+    oQ = oP + al(W * n * K * 8)
+    oT = oQ + al(W * n * K * 8)
+    G0 = g.standard_normal((W, n, n))
+    ea, eb = g.uniform(-3, 3, K), g.uniform(-2, 2, K)
+    P = g.standard_normal((W, n, K)) * 10.0 ** ea
+    Q = g.standard_normal((W, n, K)) * 10.0 ** (eb - ea)
+    buf[oG:oG + W * n * n * 8] = G0.reshape(-1).view(np.uint8)
+    buf[oP:oP + W * n * K * 8] = P.reshape(-1).view(np.uint8)
+    buf[oQ:oQ + W * n * K * 8] = Q.reshape(-1).view(np.uint8)
+    buf[oT:oT + W * 4] = np.full(W, K, np.int32).view(np.uint8)
+    st.load(tdev(buf))
+    st.flush(tdev(np.ones(W, np.uint8)))
+    G1 = st.save().cpu().numpy()[oG:oG + W * n * n * 8].view(np.float64).reshape(W, n, n)
+    worst = 0.0
+    for w in range(W):
+        for _ in range(1500):
+            l, j = g.integers(0, n, 2)          # storage row l, column j: (A^{-1})_{jl}
+            ex = Fraction(G0[w, l, j]) - sum(Fraction(P[w, j, c]) * Fraction(Q[w, l, c]) for c in range(K))
+            bound = 2.0 ** -52 * (np.abs(P[w, j]).max() * np.abs(Q[w, l]).sum() +
+                                  np.abs(P[w, j]).sum() * np.abs(Q[w, l]).max() + abs(float(ex)))
+            err = abs(float(Fraction(G1[w, l, j]) - ex))
+            worst = max(worst, err / bound)
+    assert worst <= 1.0, worst
+    assert (st.tau().cpu().numpy() == 0).all()
