@@ -122,6 +122,7 @@ struct OzWork {
     int* eS;          // W x n  power-of-two exponents of the S columns
     int* eP;          // W x n  power-of-two exponents of the panel rows
     uint8_t* go;      // W      walkers that flush now (split-product flush)
+    double* piv;      // W x n  pivots of the register panel kernel (log|det| and sign at the end)
 };
 size_t oz_work_bytes(int W, int n);
 void oz_work_carve(OzWork& Z, void* base, int W, int n);

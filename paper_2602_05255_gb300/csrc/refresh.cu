@@ -520,18 +520,14 @@ __global__ void __launch_bounds__(512, 1) k_oz_panel_rows(int n, int k0, int w0,
     __shared__ int s_pi[1024];
     __shared__ double s_wv[16];
     __shared__ int s_wi[16];
-    __shared__ double s_bv, s_log, s_sgn;
+    __shared__ double s_bv;
     __shared__ int s_bi, s_sing;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
     const int w = w0 + blockIdx.x;
     if (mask && !mask[w]) return;
     double* M = Z.M + (long long)w * n * n;
     int* perm = Z.perm + (long long)w * n;
-    if (tid == 0) {
-        s_log = k0 ? Z.logacc[w] : 0.0;
-        s_sgn = k0 ? Z.sgnacc[w] : 1.0;
-        s_sing = k0 ? Z.sing[w] : 0;
-    }
+    if (tid == 0) s_sing = k0 ? Z.sing[w] : 0;
     __syncthreads();
     for (int sp = 0; sp < OZ_B / SW; ++sp) {
         const int ks = k0 + SW * sp;
@@ -580,7 +576,7 @@ __global__ void __launch_bounds__(512, 1) k_oz_panel_rows(int n, int k0, int w0,
             __syncthreads();
             const int p = s_bi;
             if (!(s_bv > 0.0) || p < 0) {
-                if (tid == 0) { perm[k] = k; s_sing = 1; }
+                if (tid == 0) { perm[k] = k; s_sing = 1; Z.piv[(long long)w * n + k] = 0.0; }
                 continue;
             }
             if (tid == 0) perm[k] = p;
@@ -606,24 +602,27 @@ __global__ void __launch_bounds__(512, 1) k_oz_panel_rows(int n, int k0, int w0,
 #pragma unroll
                         for (int c = 0; c < SW; ++c) v[q][c] = s_bufA[c];
                 }
+                __syncthreads();   // s_bufA is reused just below
             }
-            // ---- scale the pivot row ----
+            // ---- scale the pivot row: 16 threads, one element each; the pivot
+            //      is recorded (log|det| and the sign are summed at the end) ----
 #pragma unroll
             for (int q = 0; q < RPT; ++q)
-                if (tid == tk && q == qk) {
-                    const double piv = v[q][kc];
-                    const double ip = 1.0 / piv;
+                if (tid == tk && q == qk)
 #pragma unroll
-                    for (int c = 0; c < SW; ++c) {
-                        const double x = (c == kc ? 1.0 : v[q][c]) * ip;
-                        v[q][c] = x;
-                        s_rowk[c] = x;
-                    }
-                    s_log += log(fabs(piv));
-                    const double sg = piv < 0.0 ? -s_sgn : s_sgn;
-                    s_sgn = (p != k) ? -sg : sg;
-                }
+                    for (int c = 0; c < SW; ++c) s_bufA[c] = v[q][c];
             __syncthreads();
+            if (tid < SW) {
+                const double piv = s_bufA[kc];
+                s_rowk[tid] = (tid == kc ? 1.0 : s_bufA[tid]) / piv;
+                if (tid == 0) Z.piv[(long long)w * n + k] = piv;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < RPT; ++q)
+                if (tid == tk && q == qk)
+#pragma unroll
+                    for (int c = 0; c < SW; ++c) v[q][c] = s_rowk[c];
             // ---- eliminate column k from every other row ----
 #pragma unroll
             for (int q = 0; q < RPT; ++q) {
@@ -708,11 +707,7 @@ __global__ void __launch_bounds__(512, 1) k_oz_panel_rows(int n, int k0, int w0,
             }
         }
     }
-    if (tid == 0) {
-        Z.logacc[w] = s_log;
-        Z.sgnacc[w] = s_sgn;
-        Z.sing[w] = s_sing;
-    }
+    if (tid == 0) Z.sing[w] = s_sing;
 }
 
 // Undo the row exchanges of the elimination as one column permutation of
@@ -746,10 +741,29 @@ __global__ void __launch_bounds__(RT) k_oz_finish(int n, OzWork Z, DevState<doub
         }
         __syncthreads();
     }
+    double la = 0.0;
+    int neg = 0;
+    if (n <= 1024) {
+        // log|det| = sum log|pivot|, sign = prod sign(pivot) * (-1)^(row exchanges)
+        const double* pv = Z.piv + (long long)w * n;
+        for (int k = threadIdx.x; k < n; k += RT) {
+            const double x = pv[k];
+            la += log(fabs(x));
+            neg += (x < 0.0) + (perm[k] != k);
+        }
+        la = block_sum(la, buf);
+    }
+    __shared__ int s_neg;
+    if (threadIdx.x == 0) s_neg = 0;
+    __syncthreads();
+    if (neg & 1) atomicXor(&s_neg, 1);
+    __syncthreads();
     if (threadIdx.x == 0) {
         const int sing = Z.sing[w];
-        S.logabs[w] = sing ? -INFINITY : Z.logacc[w];
-        S.sgn[w] = sing ? 0.0 : s_renorm(Z.sgnacc[w]);
+        const double lg = n <= 1024 ? la : Z.logacc[w];
+        const double sg = n <= 1024 ? (s_neg ? -1.0 : 1.0) : Z.sgnacc[w];
+        S.logabs[w] = sing ? -INFINITY : lg;
+        S.sgn[w] = sing ? 0.0 : s_renorm(sg);
         if (delayed) S.tau[w] = 0;
         S.pst[w] = sing ? 1 : 5;
     }

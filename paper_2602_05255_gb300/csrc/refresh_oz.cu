@@ -37,6 +37,7 @@
 // delayed flush.  (Two accumulator sets for an MMA / epilogue overlap do not
 // fit the 512 TMEM columns at 64 rows; at 32 rows the MMAs, whose operands
 // are re-read from shared memory per instruction, become the bound.)
+#include <algorithm>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -322,32 +323,34 @@ __global__ void k_oz_flush_go(int W, int K, const int* tau, const uint8_t* force
     go[w] = (force ? (force[w] && t > 0) : (t >= K)) ? 1 : 0;
 }
 
-// Row r of walker w's slot matrix X (rows of ldx doubles): the cu = tau * kk
-// filled slot columns times sgn, zeros after; one warp per row, slices and
-// exponent as for the panel rows.
-__global__ void __launch_bounds__(256) k_oz_slice_rows(int n, int ldx, int kk, const double* X, double sgn,
+// Rows of the walkers' slot matrices X (rows of ldx doubles): the cu =
+// tau * kk filled slot columns times sgn, zeros after; slices and exponent as
+// for the panel rows.  Persistent over walkers: on steps where no walker
+// flushes every block leaves after reading the go flags.
+__global__ void __launch_bounds__(256) k_oz_slice_rows(int W, int n, int ldx, int kk, const double* X, double sgn,
                                                        const int* tau, const uint8_t* go, uint16_t* dst, int* ex) {
-    const int w = blockIdx.y;
-    if (!go[w]) return;
-    const int lane = threadIdx.x & 31;
-    const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (r >= n) return;
-    const int cu = tau[w] * kk;
-    const double* row = X + ((long long)w * n + r) * ldx;
-    const double a = lane < cu ? sgn * row[lane] : 0.0;
-    const double b = lane + 32 < cu ? sgn * row[lane + 32] : 0.0;
-    const int mx = __reduce_max_sync(0xffffffffu, max(oz_bexp(a), oz_bexp(b)));
-    const int E = mx > 0 ? mx - 1022 : 0;
-    uint16_t ha[OZ_S], hb[OZ_S];
-    oz_digits(oz_fixed(a, E), ha);
-    oz_digits(oz_fixed(b, E), hb);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int w = blockIdx.x; w < W; w += gridDim.x) {
+        if (!go[w]) continue;
+        const int cu = tau[w] * kk;
+        for (int r = wid; r < n; r += 8) {
+            const double* row = X + ((long long)w * n + r) * ldx;
+            const double a = lane < cu ? sgn * row[lane] : 0.0;
+            const double b = lane + 32 < cu ? sgn * row[lane + 32] : 0.0;
+            const int mx = __reduce_max_sync(0xffffffffu, max(oz_bexp(a), oz_bexp(b)));
+            const int E = mx > 0 ? mx - 1022 : 0;
+            uint16_t ha[OZ_S], hb[OZ_S];
+            oz_digits(oz_fixed(a, E), ha);
+            oz_digits(oz_fixed(b, E), hb);
 #pragma unroll
-    for (int t = 0; t < OZ_S; ++t) {
-        uint16_t* d = dst + (((long long)w * OZ_S + t) * n + r) * OZ_B;
-        d[lane] = ha[t];
-        d[lane + 32] = hb[t];
+            for (int t = 0; t < OZ_S; ++t) {
+                uint16_t* d = dst + (((long long)w * OZ_S + t) * n + r) * OZ_B;
+                d[lane] = ha[t];
+                d[lane + 32] = hb[t];
+            }
+            if (lane == 0) ex[(long long)w * n + r] = E;
+        }
     }
-    if (lane == 0) ex[(long long)w * n + r] = E;
 }
 
 // ---- host side ----------------------------------------------------------------
@@ -365,6 +368,7 @@ size_t oz_work_bytes(int W, int n) {
     take(Wn * sizeof(int));                        // eS
     take(Wn * sizeof(int));                        // eP
     take((size_t)W);                               // go
+    take(Wn * sizeof(double));                     // piv
     return b;
 }
 
@@ -381,6 +385,7 @@ void oz_work_carve(OzWork& Z, void* base, int W, int n) {
     Z.eS = (int*)take(Wn * sizeof(int));
     Z.eP = (int*)take(Wn * sizeof(int));
     Z.go = (uint8_t*)take((size_t)W);
+    Z.piv = (double*)take(Wn * sizeof(double));
 }
 
 // rows x 64 BF16 matrix, box 64 x box_rows, SWIZZLE_128B
@@ -459,8 +464,9 @@ bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, co
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     k_oz_flush_go<<<(W + 255) / 256, 256, 0, st>>>(W, K, tau, force, Z.go);
-    k_oz_slice_rows<<<dim3(n / 8, W), 256, 0, st>>>(n, Kc, kk, P, 1.0, tau, Z.go, Z.Sb, Z.eS);
-    k_oz_slice_rows<<<dim3(n / 8, W), 256, 0, st>>>(n, Kc, kk, Q, -1.0, tau, Z.go, Z.Pb, Z.eP);
+    const int sgrid = std::min(W, 8 * nsm);
+    k_oz_slice_rows<<<sgrid, 256, 0, st>>>(W, n, Kc, kk, P, 1.0, tau, Z.go, Z.Sb, Z.eS);
+    k_oz_slice_rows<<<sgrid, 256, 0, st>>>(W, n, Kc, kk, Q, -1.0, tau, Z.go, Z.Pb, Z.eP);
     k_oz_gemm<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, n, (Kc + 15) / 16, Z, Z.go, err);
     return true;
 }
