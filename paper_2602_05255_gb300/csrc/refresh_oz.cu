@@ -180,9 +180,10 @@ __device__ __forceinline__ double oz_i64_to_double(long long F, int e) {
 // the epilogue of tile i runs.  Columns of the panel itself are left alone.
 constexpr int OZ_THREADS = 512;   // 16 warps: 4 per TMEM lane quarter, each 16 of the 64 rows i
 
+template <int NKS>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_oz_gemm(const __grid_constant__ OzMaps maps, int W, int w0, int n, int k0, int nks, OzWork Z,
-              const uint8_t* mask, int* err) {
+    k_oz_gemm(const __grid_constant__ OzMaps maps, int W, int w0, int n, int k0, OzWork Z, const uint8_t* mask,
+              int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -240,13 +241,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     mbar_wait(mb_tma, ph_tma);   // let copies in flight land before leaving
                 } else {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    // fully unrolled: descriptors and accumulate flags are compile-time, so
+                    // the issuing thread streams back-to-back MMAs
+                    const uint64_t a0 = desc_sw128(smem_u32(sA)), b0 = desc_sw128(smem_u32(sB));
                     uint32_t started = 0;   // bit g: accumulator g holds a partial sum
+#pragma unroll
                     for (int t = 0; t < OZ_S; ++t)
-                        for (int u = 0; u < OZ_S && u + t <= OZ_MAXLV; ++u) {
+#pragma unroll
+                        for (int u = 0; u < OZ_S; ++u) {
+                            if (u + t > OZ_MAXLV) continue;
                             const int g = min(t + u, OZ_GROUPS - 1);   // level t+u+2: 2 .. 6, then 7..10
-                            const uint64_t a = desc_sw128(smem_u32(sA + t * OZ_SLICE_A));
-                            const uint64_t b = desc_sw128(smem_u32(sB + u * OZ_SLICE_B));
-                            for (int ks = 0; ks < nks; ++ks) {
+                            const uint64_t a = a0 + (uint64_t)((t * OZ_SLICE_A) >> 4);
+                            const uint64_t b = b0 + (uint64_t)((u * OZ_SLICE_B) >> 4);
+#pragma unroll
+                            for (int ks = 0; ks < NKS; ++ks) {
                                 const uint64_t adv = (uint64_t)(ks * 32) >> 4;   // 16 BF16 along K per MMA
                                 oz_mma(tmem + 64u * g, a + adv, b + adv, (started >> g) & 1u);
                                 started |= 1u << g;
@@ -412,7 +420,8 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
     OzMaps maps;
     if (!oz_map(&maps.S, Z.Sb, rows, OZ_TJ) || !oz_map(&maps.P, Z.Pb, rows, OZ_TI)) return false;
     const size_t dyn = 1024 + (size_t)OZ_S * (OZ_SLICE_A + OZ_SLICE_B);
-    if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_oz_gemm<OZ_B / 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
+        cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -426,7 +435,7 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
         if (hook) { hook(hctx, 4, 0); hook(hctx, 5, 1); }
         k_oz_slice_P<<<dim3(n / 8, W), 256, 0, st>>>(n, k0, 0, Z, mask);
         k_oz_slice_S<<<dim3(n / 64, W), 256, 0, st>>>(n, k0, 0, Z, mask);
-        k_oz_gemm<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, k0, OZ_B / 16, Z, mask, err);
+        k_oz_gemm<OZ_B / 16><<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, k0, Z, mask, err);
         if (hook) hook(hctx, 5, 0);
     }
     launch_oz_finish(W, n, Z, S, mask, delayed, st);
@@ -454,7 +463,10 @@ bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, co
     const size_t dyn = 1024 + (size_t)OZ_S * (OZ_SLICE_A + OZ_SLICE_B);
     static thread_local bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
+        bool ok = true;
+        for (auto kern : {k_oz_gemm<1>, k_oz_gemm<2>, k_oz_gemm<3>, k_oz_gemm<4>})
+            ok = ok && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) == cudaSuccess;
+        if (!ok) {
             cudaGetLastError();
             return false;
         }
@@ -467,7 +479,14 @@ bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, co
     const int sgrid = std::min(W, 8 * nsm);
     k_oz_slice_rows<<<sgrid, 256, 0, st>>>(W, n, Kc, kk, P, 1.0, tau, Z.go, Z.Sb, Z.eS);
     k_oz_slice_rows<<<sgrid, 256, 0, st>>>(W, n, Kc, kk, Q, -1.0, tau, Z.go, Z.Pb, Z.eP);
-    k_oz_gemm<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, n, (Kc + 15) / 16, Z, Z.go, err);
+    auto kern = k_oz_gemm<1>;
+    switch ((Kc + 15) / 16) {
+        case 2: kern = k_oz_gemm<2>; break;
+        case 3: kern = k_oz_gemm<3>; break;
+        case 4: kern = k_oz_gemm<4>; break;
+        default: break;
+    }
+    kern<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, n, Z, Z.go, err);
     return true;
 }
 
