@@ -251,6 +251,13 @@ def refresh_roofline(prof, n, W, bf16_sustained):
             "flop_per_launch": 2.0 * n ** 3 * W, "ms_per_launch": per, "peak_source": fp64_src}
 
 
+# DRAM bytes per walker of one rank-1 delayed accept launch at n = 1024, from an
+# ncu capture of k_accept_delayed_lane<double> at 64 walkers (545.8 MB read +
+# 4.0 MB written): the traffic scales with the walkers (one pass over each
+# A_0^{-1}), so a full launch is this times W.
+ACCEPT_DELAYED_TRAFFIC_PER_WALKER_N1024 = (545.827584e6 + 4.03712e6) / 64
+
+
 def accept_roofline(delay, arith, n, W, ms, hbm):
     """Roofline of one accept launch (one walker-update of every walker).
 
@@ -265,8 +272,10 @@ def accept_roofline(delay, arith, n, W, ms, hbm):
     flop_per = (4 if delay < 2 else 2) * n * n * W
     t_hbm = bytes_per / (hbm * 1e9)
     t_fp64 = flop_per / (FP64_PEAK_TFLOPS * 1e12)
+    traffic = ACCEPT_DELAYED_TRAFFIC_PER_WALKER_N1024 * W if (delay >= 2 and arith == "native" and n == 1024) \
+        else None
     out = {"bytes_per_launch": bytes_per, "fp64_flop_per_launch": flop_per if arith == "native" else 0,
-           "ms_per_launch": ms, "traffic": None,
+           "ms_per_launch": ms, "traffic": traffic,
            "hbm": {"achieved": bytes_per / (ms / 1e3) / 1e9 if ms else None, "peak": hbm, "unit": "GB/s"},
            "time_at_hbm_peak_ms": t_hbm * 1e3, "time_at_fp64_peak_ms": t_fp64 * 1e3}
     out["hbm"]["frac"] = out["hbm"]["achieved"] / hbm if ms else None
