@@ -96,8 +96,9 @@ typedef enum {
  * n x n x 64 product; LRU_REFRESH_TENSOR runs it on the BF16 tensor cores as
  * an exact split product (7 slices of 8 bits per operand, FP64 recombination:
  * the accuracy of an FP64 update), the panels themselves in FP64.  It applies
- * to uniform n with n % 128 == 0, 128 <= n <= 2048, W <= 65535, and to calls
- * that do not ask for the drift; other calls use LRU_REFRESH_FP64. */
+ * to uniform n with n % 128 == 0, 128 <= n <= 2048 and W <= 65535; other
+ * handles use LRU_REFRESH_FP64.  A refresh that asks for the drift allocates,
+ * on first use, a second W x n x n workspace for the fresh inverses. */
 typedef enum {
     LRU_REFRESH_AUTO = 0,     /* the tensor-core form where it applies */
     LRU_REFRESH_FP64 = 1,     /* blocked Gauss-Jordan entirely on the FP64 pipe */

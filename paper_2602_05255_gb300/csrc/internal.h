@@ -129,14 +129,16 @@ void oz_work_carve(OzWork& Z, void* base, int W, int n);
 void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mask, cudaStream_t st);
 void launch_oz_panel(int W, int w0, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st);
 void launch_oz_finish(int W, int n, const OzWork& Z, const DevState<double>& S, const uint8_t* mask, bool delayed,
-                      cudaStream_t st);
+                      bool reset_tau, cudaStream_t st);
+void launch_oz_drift_store(int W, int n, const DevLayout& L, const DevState<double>& S, const double* M,
+                           const uint8_t* mask, double* drift, bool delayed, cudaStream_t st);
 // delayed determinant flush A_0^{-1} -= P Q^T as the same exact split product
 // (uniform n, n % 128 == 0, Kc <= 64); walkers with tau >= K, or force && tau > 0
 bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, const double* Q, const int* tau,
                         const uint8_t* force, const OzWork& Z, int* err, cudaStream_t st);
 // hook(ctx, class, begin) brackets the panel (class 4) and update (class 5) launches
 bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const DevState<double>& S,
-                       const uint8_t* mask, bool delayed, int* err, cudaStream_t st,
+                       const uint8_t* mask, bool delayed, bool reset_tau, int* err, cudaStream_t st,
                        void (*hook)(void*, int, int), void* hctx);
 void launch_wait_selftest(const int* flag, long long iters, int* err, cudaStream_t st);
 void launch_commit_moves(int W, int n, int k, int* occ, const int* slot, const int* newrow, const uint8_t* mask,

@@ -87,6 +87,8 @@ struct lru_ctx {
     // workspace of the tensor-core refresh (allocated on first use)
     void* ozw = nullptr;
     size_t oz_bytes = 0;
+    void* ozM = nullptr;         // fresh inverses when the drift is asked for
+    size_t ozM_bytes = 0;
     bool oz_ok = false;          // the tensor-core refresh applies to this handle
     // adjoint workspace (allocated on first use)
     void* bws = nullptr;
@@ -411,6 +413,7 @@ lru_status lru_destroy(lru_handle h) {
     if (h->ws) cudaFree(h->ws);
     if (h->bws) cudaFree(h->bws);
     if (h->ozw) cudaFree(h->ozw);
+    if (h->ozM) cudaFree(h->ozM);
     for (auto& v : h->prof_ev)
         for (auto& e : v) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     cudaGetLastError();
@@ -426,7 +429,7 @@ lru_status lru_set_stream(lru_handle h, void* stream) {
 
 lru_status lru_device_bytes(lru_handle h, size_t* bytes) {
     if (!h || !bytes) return LRU_ERR_ARG;
-    *bytes = h->bytes + (h->ws ? (size_t)h->nws * h->n_max * h->n_max * dtype_size(h->dtype) : 0) + h->oz_bytes;
+    *bytes = h->bytes + (h->ws ? (size_t)h->nws * h->n_max * h->n_max * dtype_size(h->dtype) : 0) + h->oz_bytes + h->ozM_bytes;
     return LRU_OK;
 }
 
@@ -452,17 +455,29 @@ static lru_status do_init(lru_handle h, const void* A, const uint8_t* mask, doub
                           void* sign_out, bool with_ws) {
     if (!A) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
-    if (h->oz_ok && !drift) {
-        // FP64 panels + tensor-core trailing updates, in place in the state
+    if (h->oz_ok) {
+        // FP64 panels + tensor-core trailing updates: in place in the state, or
+        // (drift asked for) into a workspace compared with the tracked inverse
         lru_status s = ensure_oz(h);
         if (s != LRU_OK) return s;
+        if (drift && !h->ozM) {
+            const size_t b = (size_t)h->W * h->n_uni * h->n_uni * sizeof(double);
+            if (cudaMalloc(&h->ozM, b) != cudaSuccess) {
+                cudaGetLastError();
+                h->ozM = nullptr;
+                return LRU_ERR_NOMEM;
+            }
+            h->ozM_bytes = b;
+        }
         OzWork Z{};
         oz_work_carve(Z, h->ozw, h->W, h->n_uni);
-        Z.M = (double*)h->G;
+        Z.M = drift ? (double*)h->ozM : (double*)h->G;
         DevState<double> S = h->state<double>();
         prof_begin(h, LRU_PROF_REFRESH);
-        const bool ok = launch_refresh_oz(h->W, h->n_uni, (const double*)A, Z, S, mask, h->delayed, h->err,
-                                          h->stream, h->prof_on ? oz_prof_hook : nullptr, h);
+        bool ok = launch_refresh_oz(h->W, h->n_uni, (const double*)A, Z, S, mask, h->delayed, !drift, h->err,
+                                    h->stream, h->prof_on ? oz_prof_hook : nullptr, h);
+        if (ok && drift)
+            launch_oz_drift_store(h->W, h->n_uni, h->layout(), S, Z.M, mask, drift, h->delayed, h->stream);
         prof_end(h, LRU_PROF_REFRESH);
         if (ok) {
             h->launches += 2 + 4 * (h->n_uni / OZ_B);

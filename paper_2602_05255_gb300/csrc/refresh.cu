@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(512, 1) k_oz_panel_rows(int n, int k0, int w0,
 // four rows at a time through shared memory; then log|det|, sign and the
 // fresh-state flags.
 __global__ void __launch_bounds__(RT) k_oz_finish(int n, OzWork Z, DevState<double> S, const uint8_t* mask,
-                                                  bool delayed) {
+                                                  bool delayed, bool reset_tau) {
     extern __shared__ __align__(16) unsigned char dsm[];
     double* buf = reinterpret_cast<double*>(dsm);
     int* idx = reinterpret_cast<int*>(buf + 4 * n);
@@ -764,9 +764,49 @@ __global__ void __launch_bounds__(RT) k_oz_finish(int n, OzWork Z, DevState<doub
         const double sg = n <= 1024 ? (s_neg ? -1.0 : 1.0) : Z.sgnacc[w];
         S.logabs[w] = sing ? -INFINITY : lg;
         S.sgn[w] = sing ? 0.0 : s_renorm(sg);
-        if (delayed) S.tau[w] = 0;
+        if (delayed && reset_tau) S.tau[w] = 0;
         S.pst[w] = sing ? 1 : 5;
     }
+}
+
+// Drift of the tracked inverse against the fresh one in M (relative
+// Frobenius norm; the delayed form's pending slots are applied on the fly,
+// A^{-1} = A_0^{-1} - P Q^T), then M replaces the state and tau is reset.
+__global__ void __launch_bounds__(RT) k_oz_drift_store(int n, DevLayout L, DevState<double> S, const double* M,
+                                                       const uint8_t* mask, double* drift, bool delayed) {
+    __shared__ double s_red[32];
+    const int w = blockIdx.x;
+    if (mask && !mask[w]) return;
+    const long long off = (long long)w * n * n;
+    const long long vo = (long long)w * n;
+    const int cu = delayed ? S.tau[w] * L.kk : 0;
+    double num = 0.0, den = 0.0;
+    for (long long e = threadIdx.x; e < (long long)n * n; e += RT) {
+        const int l = (int)(e / n), j = (int)(e % n);   // storage [l * n + j] = (A^{-1})_{jl}
+        double tr = S.G[off + e];
+        if (cu) {
+            const double* pr = S.P + (vo + j) * L.Kc;
+            const double* qr = S.Q + (vo + l) * L.Kc;
+            double sm = 0.0;
+            for (int c = 0; c < cu; ++c) sm = fma(pr[c], qr[c], sm);
+            tr -= sm;
+        }
+        const double f = M[off + e];
+        num += (tr - f) * (tr - f);
+        den += f * f;
+        S.G[off + e] = f;
+    }
+    num = block_sum(num, s_red);
+    den = block_sum(den, s_red);
+    if (threadIdx.x == 0) {
+        if (drift) drift[w] = den > 0 ? sqrt(num / den) : 0.0;
+        if (delayed) S.tau[w] = 0;
+    }
+}
+
+void launch_oz_drift_store(int W, int n, const DevLayout& L, const DevState<double>& S, const double* M,
+                           const uint8_t* mask, double* drift, bool delayed, cudaStream_t st) {
+    k_oz_drift_store<<<W, RT, 0, st>>>(n, L, S, M, mask, drift, delayed);
 }
 
 void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mask, cudaStream_t st) {
@@ -788,10 +828,10 @@ void launch_oz_panel(int W, int w0, int n, int k0, const OzWork& Z, const uint8_
 }
 
 void launch_oz_finish(int W, int n, const OzWork& Z, const DevState<double>& S, const uint8_t* mask, bool delayed,
-                      cudaStream_t st) {
+                      bool reset_tau, cudaStream_t st) {
     const int dyn = (int)(4 * n * sizeof(double) + n * sizeof(int));
     cudaFuncSetAttribute(k_oz_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-    k_oz_finish<<<W, RT, dyn, st>>>(n, Z, S, mask, delayed);
+    k_oz_finish<<<W, RT, dyn, st>>>(n, Z, S, mask, delayed, reset_tau);
 }
 
 #define LRU_INST_R(T)                                                                                       \

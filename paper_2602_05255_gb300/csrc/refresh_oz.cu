@@ -413,7 +413,7 @@ static bool oz_map(CUtensorMap* m, const void* base, long long rows, int box_row
 // A^{-1} storage), n / 64 panels, then the column permutation and log|det|.
 // Needs n % 128 == 0, 128 <= n <= 2048 and W <= 65535 (checked by the caller).
 bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const DevState<double>& S,
-                       const uint8_t* mask, bool delayed, int* err, cudaStream_t st,
+                       const uint8_t* mask, bool delayed, bool reset_tau, int* err, cudaStream_t st,
                        void (*hook)(void*, int, int), void* hctx) {
     const long long rows = (long long)W * OZ_S * n;
     if (rows >= (1ll << 31)) return false;
@@ -438,7 +438,7 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
         k_oz_gemm<OZ_B / 16><<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, k0, Z, mask, err);
         if (hook) hook(hctx, 5, 0);
     }
-    launch_oz_finish(W, n, Z, S, mask, delayed, st);
+    launch_oz_finish(W, n, Z, S, mask, delayed, reset_tau, st);
     return true;
 }
 

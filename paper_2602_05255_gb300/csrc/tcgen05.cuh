@@ -1,7 +1,7 @@
 // Inline-PTX helpers for the tcgen05 / TMA kernels (sm_103a): shared-memory
 // addresses, mbarriers with bounded waits, 2-D TMA tile loads, UMMA shared
 // memory descriptors (K-major, SWIZZLE_128B), MMA completion and TMEM loads;
-// and the host lookup of the driver's tensor-map encoder.
+// and the host lookup of the CUDA driver's tensor-map encoder.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>

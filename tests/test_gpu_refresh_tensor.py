@@ -121,3 +121,38 @@ def test_delayed_chain_with_tensor_refresh_matches_oracle():
         check_ratios(ratios[:, w], chain, exact, what=w)
         assert fro_rel(inv[w], O.carrier_inverse(car)) <= 1e-10
     st.check_device_error()
+
+
+def test_tensor_refresh_with_drift_and_mask():
+    # the drift (tracked inverse with its pending slots vs the fresh one) and the
+    # state after the refresh, tensor-core form against the all-FP64 form
+    L = lrugb()
+    W, n, K, steps = 4, 256, 8, 13           # one flush, then 5 pending slots
+    Phi, occ0, slot, new = det_workload(861, W, n, 2 * n, steps)
+    out = {}
+    for mode in (L.REFRESH_TENSOR, L.REFRESH_FP64):
+        st = L.LowRankState("det", W, n, k=1, dtype=torch.float64, delay=K, refresh=mode)
+        Phi_d, occ_d = tdev(Phi), tdev(occ0)
+        st.init(st.gather_rows(Phi_d, occ_d))
+        slot_d, new_d = tdev(slot), tdev(new)
+        for s in range(steps):
+            V, idx = st.form_row_moves(Phi_d, occ_d, slot_d[s], new_d[s])
+            st.propose_det(L.Operand(idx=idx, onehot_mask=1), L.Operand(dense=V))
+            st.accept()
+            st.commit_moves(occ_d, slot_d[s], new_d[s])
+        before = st.inverse().cpu().numpy()
+        mask = np.array([1, 0, 1, 1], np.uint8)
+        A = st.gather_rows(Phi_d, occ_d)
+        drift = st.refresh(A, tdev(mask)).cpu().numpy()
+        out[mode] = (drift, before, st.inverse().cpu().numpy(), st.tau().cpu().numpy(), A.cpu().numpy())
+        st.check_device_error()
+    d_tc, before, after, tau, A = out[L.REFRESH_TENSOR]
+    d_fp = out[L.REFRESH_FP64][0]
+    for w in range(W):
+        if mask[w]:
+            assert fro_rel(after[w], O.inv(A[w])) <= 1e-10
+            assert tau[w] == 0
+            assert 0 < d_tc[w] <= 1e-9 and abs(d_tc[w] - d_fp[w]) <= max(1e-13, 0.1 * d_fp[w])
+        else:
+            assert np.isnan(d_tc[w]) and tau[w] == steps % K
+            assert np.array_equal(after[w], before[w])
