@@ -124,10 +124,18 @@ struct OzWork {
     uint8_t* go;      // W      walkers that flush now (split-product flush)
     double* piv;      // W x n  pivots of the register panel kernel (log|det| and sign at the end)
 };
+// columns a split-product update writes: [c_lo, c_hi) minus [s_lo, s_hi), in
+// the 128-column tiles jt_lo .. jt_hi - 1
+struct OzCols {
+    int c_lo, c_hi, s_lo, s_hi, jt_lo, jt_hi;
+};
 size_t oz_work_bytes(int W, int n);
 void oz_work_carve(OzWork& Z, void* base, int W, int n);
 void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mask, cudaStream_t st);
 void launch_oz_panel(int W, int w0, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st);
+// one 16-column sub-panel (n <= 1024): elimination and its row exchanges on the
+// other panel columns; the last one of a panel also exchanges the outside columns
+bool launch_oz_subpanel(int W, int n, int k0, int sp, const OzWork& Z, const uint8_t* mask, cudaStream_t st);
 void launch_oz_finish(int W, int n, const OzWork& Z, const DevState<double>& S, const uint8_t* mask, bool delayed,
                       bool reset_tau, cudaStream_t st);
 void launch_oz_drift_store(int W, int n, const DevLayout& L, const DevState<double>& S, const double* M,

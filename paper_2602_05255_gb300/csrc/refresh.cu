@@ -504,32 +504,31 @@ __global__ void __launch_bounds__(RT) k_oz_panel(int n, int k0, int w0, OzWork Z
     }
 }
 
-// The same panel step with the rows in registers (n <= 1024): thread t owns
-// rows t + q * blockDim (q < RPT, blockDim = n / RPT).  Each 16-column
-// sub-panel is eliminated in registers (pivot by a block reduction, row
-// swaps through shared memory); its transform then updates the other 48
-// panel columns, M[r][j] = M[pi(r)][j] + sum_c (T - E)[r][c] S[c][j], with
-// the sub-panel's row exchanges folded in as the gather pi and the 16 pivot
-// rows S staged in shared memory.
+// One 16-column sub-panel of panel [k0, k0 + OZ_B) with the rows in registers
+// (n <= 1024): thread t owns rows t + q * blockDim (q < RPT, blockDim = n /
+// RPT).  The sub-panel is eliminated in registers (pivot by a block reduction,
+// row swaps through shared memory) and its transform columns written back;
+// its row exchanges are then applied to the other panel columns, whose update
+// by the transform is a split product on the tensor cores (refresh_oz.cu).
+// The last sub-panel of a panel also applies the panel's exchanges, in pivot
+// order, to the columns outside it.  Pivots go to Z.piv (log|det| and the
+// sign are summed at the end).
 template <int RPT>
-__global__ void __launch_bounds__(512, 1) k_oz_panel_rows(int n, int k0, int w0, OzWork Z, const uint8_t* mask) {
+__global__ void __launch_bounds__(512, 1) k_oz_subpanel_rows(int n, int k0, int sp, OzWork Z, const uint8_t* mask) {
     constexpr int SW = 16;                   // sub-panel width
-    constexpr int NO = OZ_B - SW;            // other panel columns per sub-panel
-    __shared__ double s_S[SW][NO + 1];
     __shared__ double s_rowk[SW], s_bufA[SW], s_bufB[SW];
-    __shared__ int s_pi[1024];
     __shared__ double s_wv[16];
     __shared__ int s_wi[16];
     __shared__ double s_bv;
     __shared__ int s_bi, s_sing;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
-    const int w = w0 + blockIdx.x;
+    const int w = blockIdx.x;
     if (mask && !mask[w]) return;
     double* M = Z.M + (long long)w * n * n;
     int* perm = Z.perm + (long long)w * n;
-    if (tid == 0) s_sing = k0 ? Z.sing[w] : 0;
+    if (tid == 0) s_sing = (k0 || sp) ? Z.sing[w] : 0;
     __syncthreads();
-    for (int sp = 0; sp < OZ_B / SW; ++sp) {
+    {
         const int ks = k0 + SW * sp;
         double v[RPT][SW];
 #pragma unroll
@@ -641,62 +640,22 @@ __global__ void __launch_bounds__(512, 1) k_oz_panel_rows(int n, int k0, int w0,
 #pragma unroll
             for (int c = 0; c < SW / 2; ++c) dst[c] = make_double2(v[q][2 * c], v[q][2 * c + 1]);
         }
-        // ---- row gather of this sub-panel's exchanges, pivot rows S ----
-        for (int r = tid; r < n; r += nt) s_pi[r] = r;
         __syncthreads();
-        if (tid == 0)
+        // ---- this sub-panel's exchanges on the other panel columns ----
+        for (int t = tid; t < OZ_B - SW; t += nt) {
+            const int col = k0 + t + (t >= SW * sp ? SW : 0);
             for (int kc = 0; kc < SW; ++kc) {
-                const int k = ks + kc, p = perm[k];
-                if (p != k) { const int t = s_pi[k]; s_pi[k] = s_pi[p]; s_pi[p] = t; }
-            }
-        __syncthreads();
-        for (int e = tid; e < SW * NO; e += nt) {
-            const int c = e / NO, jj = e % NO;
-            const int col = k0 + jj + (jj >= SW * sp ? SW : 0);
-            s_S[c][jj] = M[(long long)s_pi[ks + c] * n + col];
-        }
-        // (T - E): the identity comes off the pivot rows' own columns
-#pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-            const int r = tid + q * nt;
-#pragma unroll
-            for (int c = 0; c < SW; ++c)
-                if (r == ks + c) v[q][c] -= 1.0;
-        }
-        __syncthreads();
-        // ---- update of the other panel columns, CW at a time ----
-        constexpr int CW = RPT == 1 ? 8 : 4;
-        for (int ch = 0; ch < NO / CW; ++ch) {
-            const int jj0 = CW * ch;
-            const int col0 = k0 + jj0 + (jj0 >= SW * sp ? SW : 0);
-            double o[RPT][CW];
-#pragma unroll
-            for (int q = 0; q < RPT; ++q) {
-                const double2* src =
-                    reinterpret_cast<const double2*>(M + (long long)s_pi[tid + q * nt] * n + col0);
-#pragma unroll
-                for (int x = 0; x < CW / 2; ++x) {
-                    const double2 y = src[x];
-                    o[q][2 * x] = y.x;
-                    o[q][2 * x + 1] = y.y;
+                const int kk = ks + kc, p = perm[kk];
+                if (p != kk) {
+                    const double a = M[(long long)kk * n + col];
+                    M[(long long)kk * n + col] = M[(long long)p * n + col];
+                    M[(long long)p * n + col] = a;
                 }
             }
-            __syncthreads();   // every old row is read before any row is written
-#pragma unroll
-            for (int q = 0; q < RPT; ++q) {
-#pragma unroll
-                for (int c = 0; c < SW; ++c)
-#pragma unroll
-                    for (int x = 0; x < CW; ++x) o[q][x] = fma(v[q][c], s_S[c][jj0 + x], o[q][x]);
-                double2* dst = reinterpret_cast<double2*>(M + (long long)(tid + q * nt) * n + col0);
-#pragma unroll
-                for (int x = 0; x < CW / 2; ++x) dst[x] = make_double2(o[q][2 * x], o[q][2 * x + 1]);
-            }
         }
-        __syncthreads();
     }
-    // ---- the panel's exchanges on the columns outside it, in pivot order ----
-    for (int j = tid; j < n; j += nt) {
+    // ---- last sub-panel: the panel's exchanges on the columns outside it ----
+    for (int j = tid; j < n && sp == OZ_B / SW - 1; j += nt) {
         if (j >= k0 && j < k0 + OZ_B) continue;
         for (int kc = 0; kc < OZ_B; ++kc) {
             const int k = k0 + kc, p = perm[k];
@@ -813,15 +772,19 @@ void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mas
     k_oz_load<<<dim3(n / 32, n / 32, W), dim3(32, 8), 0, st>>>(n, A, M, mask);
 }
 
-void launch_oz_panel(int W, int w0, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st) {
+bool launch_oz_subpanel(int W, int n, int k0, int sp, const OzWork& Z, const uint8_t* mask, cudaStream_t st) {
     if (n <= 512) {
-        k_oz_panel_rows<1><<<W, n, 0, st>>>(n, k0, w0, Z, mask);
-        return;
+        k_oz_subpanel_rows<1><<<W, n, 0, st>>>(n, k0, sp, Z, mask);
+        return true;
     }
     if (n <= 1024) {
-        k_oz_panel_rows<2><<<W, n / 2, 0, st>>>(n, k0, w0, Z, mask);
-        return;
+        k_oz_subpanel_rows<2><<<W, n / 2, 0, st>>>(n, k0, sp, Z, mask);
+        return true;
     }
+    return false;
+}
+
+void launch_oz_panel(int W, int w0, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st) {
     const int dyn = (int)sizeof(GJSmem<double>);
     cudaFuncSetAttribute(k_oz_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     k_oz_panel<<<W, RT, dyn, st>>>(n, k0, w0, Z, mask);

@@ -3,10 +3,12 @@
 // The refresh (Sec. 2.3 init_det_carrier; Sec. 1 advises double precision) is
 // a blocked Gauss-Jordan inversion of M = A^T, n^3 FMAs per walker, and
 // GB300's FP64 pipe runs at about 1/64 of its FP32 rate.  Panels of OZ_B = 64
-// columns are eliminated in FP64 (refresh.cu: n * 64^2 FMAs per panel); the
-// update of every other column by the panel,
+// columns are eliminated in four 16-column sub-panels: each in FP64
+// (refresh.cu: n * 16^2 FMAs), its update of the panel's other 48 columns as
+// the split product below with K = 16 (for n > 1024 the whole panel stays in
+// FP64); then the update of every other column by the panel,
 //     M[i, j] += sum_c (Pan - E)[i, c] * S[c, j],   S = rows k0 .. k0+63 of M,
-// (n^2 * 64 FMAs per panel: 94% of the work at n = 1024) runs as an
+// (n^2 * 64 FMAs per panel: 94% of the work at n = 1024) also runs as an
 // error-free split product on the BF16 tensor cores, the scheme of Ozaki,
 // Ogita, Oishi and Rump (Numer. Algorithms 59, 2012):
 //   - every 64-vector (a row of Pan - E, a column of S) is scaled by a power
@@ -92,18 +94,20 @@ __device__ __forceinline__ void oz_digits(long long X, uint16_t (&h)[OZ_S]) {
     }
 }
 
-// Rows of (Pan - E): row i of walker w, columns k0 .. k0+63 of M, minus 1 at
-// (k0 + c, c).  One warp per row; lane covers c = lane and lane + 32.
-__global__ void __launch_bounds__(256) k_oz_slice_P(int n, int k0, int w0, OzWork Z, const uint8_t* mask) {
+// Rows of (Pan - E): row i of walker w, the width (<= 64) columns c0 .. of M,
+// minus 1 at (c0 + c, c); columns past the width are zero.  One warp per row;
+// lane covers c = lane and lane + 32.
+__global__ void __launch_bounds__(256) k_oz_slice_P(int n, int c0, int width, int w0, OzWork Z,
+                                                    const uint8_t* mask) {
     const int w = w0 + blockIdx.y;
     if (mask && !mask[w]) return;
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (i >= n) return;
-    const double* row = Z.M + (long long)w * n * n + (long long)i * n + k0;
-    double a = row[lane], b = row[lane + 32];
-    if (i == k0 + lane) a -= 1.0;
-    if (i == k0 + lane + 32) b -= 1.0;
+    const double* row = Z.M + (long long)w * n * n + (long long)i * n + c0;
+    double a = lane < width ? row[lane] : 0.0, b = lane + 32 < width ? row[lane + 32] : 0.0;
+    if (lane < width && i == c0 + lane) a -= 1.0;
+    if (lane + 32 < width && i == c0 + lane + 32) b -= 1.0;
     const int mx = __reduce_max_sync(0xffffffffu, max(oz_bexp(a), oz_bexp(b)));
     const int E = mx > 0 ? mx - 1022 : 0;
     uint16_t ha[OZ_S], hb[OZ_S];
@@ -118,17 +122,19 @@ __global__ void __launch_bounds__(256) k_oz_slice_P(int n, int k0, int w0, OzWor
     if (lane == 0) Z.eP[(long long)w * n + i] = E;
 }
 
-// Columns of S = rows k0 .. k0+63 of M: a 64 x 64 block per CTA through shared
-// memory (stored transposed), then one warp per column j.
-__global__ void __launch_bounds__(256) k_oz_slice_S(int n, int k0, int w0, OzWork Z, const uint8_t* mask) {
+// Columns of S = the nr (<= 64) rows r0 .. of M, zero past nr: a 64 x 64
+// block per CTA (column blocks jb0, jb0 + 1, ..) through shared memory
+// (stored transposed), then one warp per column j.
+__global__ void __launch_bounds__(256) k_oz_slice_S(int n, int r0, int nr, int jb0, int w0, OzWork Z,
+                                                    const uint8_t* mask) {
     __shared__ double sT[64][65];   // sT[j][c] = S[c][j0 + j]
     const int w = w0 + blockIdx.y;
     if (mask && !mask[w]) return;
-    const int j0 = blockIdx.x * 64;
+    const int j0 = (jb0 + blockIdx.x) * 64;
     const double* M = Z.M + (long long)w * n * n;
     for (int e = threadIdx.x; e < 64 * 64; e += 256) {
         const int c = e >> 6, j = e & 63;
-        sT[j][c] = M[(long long)(k0 + c) * n + j0 + j];
+        sT[j][c] = c < nr ? M[(long long)(r0 + c) * n + j0 + j] : 0.0;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -182,8 +188,8 @@ constexpr int OZ_THREADS = 512;   // 16 warps: 4 per TMEM lane quarter, each 16 
 
 template <int NKS>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_oz_gemm(const __grid_constant__ OzMaps maps, int W, int w0, int n, int k0, OzWork Z, const uint8_t* mask,
-              int* err) {
+    k_oz_gemm(const __grid_constant__ OzMaps maps, int W, int w0, int n, OzCols cols, OzWork Z,
+              const uint8_t* mask, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -210,13 +216,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const uint32_t tmem = s_tmem;
     const uint32_t mb_tma = smem_u32(&mbar[0]), mb_mma = smem_u32(&mbar[1]);
     const uint32_t bytes_a = (uint32_t)OZ_S * OZ_SLICE_A, bytes_b = (uint32_t)OZ_S * OZ_SLICE_B;
-    const int ntj = n / OZ_TJ, nti = n / OZ_TI;
+    const int ntj = cols.jt_hi - cols.jt_lo, nti = n / OZ_TI;
     const long long units = (long long)W * ntj;
     uint32_t ph_tma = 0, ph_mma = 0;
     for (long long un = blockIdx.x; un < units && !s_abort; un += gridDim.x) {
         const int w = w0 + (int)(un / ntj);
         if (mask && !mask[w]) continue;
-        const int j0 = (int)(un % ntj) * OZ_TJ;
+        const int j0 = (cols.jt_lo + (int)(un % ntj)) * OZ_TJ;
         const int ys = (int)((long long)w * OZ_S * n);
         if (tid == 0) {
             mbar_expect_tx(mb_tma, bytes_a + bytes_b);
@@ -228,7 +234,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         // per thread of the epilogue: column j (TMEM lane) and its scale
         const int quad = warp & 3, part = warp >> 2;
         const int j = j0 + 32 * quad + lane;
-        const bool keep = !(j >= k0 && j < k0 + OZ_B);
+        const bool keep = j >= cols.c_lo && j < cols.c_hi && !(j >= cols.s_lo && j < cols.s_hi);
+        const bool wact = __any_sync(0xffffffffu, keep);   // a warp with no column to write skips its epilogue
         const int eSj = Z.eS[(long long)w * n + j];
         double* Mw = Z.M + (long long)w * n * n;
         const int* eP = Z.eP + (long long)w * n;
@@ -288,7 +295,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             // ---- epilogue: warp q reads TMEM lanes 32 (q % 4) .. +31 (columns j),
             //      and rows i0 + 16 (q / 4) .. +15 in two chunks of 8 ----
 #pragma unroll
-            for (int ch = 0; ch < 2; ++ch) {
+            for (int ch = 0; ch < 2 && wact; ++ch) {
                 const int c0 = 16 * part + 8 * ch;
                 float acc[OZ_GROUPS][8];
 #pragma unroll
@@ -421,7 +428,8 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
     if (!oz_map(&maps.S, Z.Sb, rows, OZ_TJ) || !oz_map(&maps.P, Z.Pb, rows, OZ_TI)) return false;
     const size_t dyn = 1024 + (size_t)OZ_S * (OZ_SLICE_A + OZ_SLICE_B);
     if (cudaFuncSetAttribute(k_oz_gemm<OZ_B / 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
-        cudaSuccess) {
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_oz_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -429,13 +437,29 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     launch_oz_load(W, n, A, Z.M, mask, st);
+    constexpr int SW = 16;   // sub-panel width
     for (int k0 = 0; k0 < n; k0 += OZ_B) {
         if (hook) hook(hctx, 4, 1);
-        launch_oz_panel(W, 0, n, k0, Z, mask, st);
+        if (n <= 1024) {
+            // sub-panels: FP64 elimination, then the update of the other panel
+            // columns as a K = 16 split product on the panel's 128-column tile
+            const int jt = k0 / OZ_TJ;
+            for (int sp = 0; sp < OZ_B / SW; ++sp) {
+                const int ks = k0 + SW * sp;
+                launch_oz_subpanel(W, n, k0, sp, Z, mask, st);
+                k_oz_slice_P<<<dim3(n / 8, W), 256, 0, st>>>(n, ks, SW, 0, Z, mask);
+                k_oz_slice_S<<<dim3(OZ_TJ / 64, W), 256, 0, st>>>(n, ks, SW, jt * (OZ_TJ / 64), 0, Z, mask);
+                const OzCols inner{k0, k0 + OZ_B, ks, ks + SW, jt, jt + 1};
+                k_oz_gemm<1><<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, inner, Z, mask, err);
+            }
+        } else {
+            launch_oz_panel(W, 0, n, k0, Z, mask, st);
+        }
         if (hook) { hook(hctx, 4, 0); hook(hctx, 5, 1); }
-        k_oz_slice_P<<<dim3(n / 8, W), 256, 0, st>>>(n, k0, 0, Z, mask);
-        k_oz_slice_S<<<dim3(n / 64, W), 256, 0, st>>>(n, k0, 0, Z, mask);
-        k_oz_gemm<OZ_B / 16><<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, k0, Z, mask, err);
+        k_oz_slice_P<<<dim3(n / 8, W), 256, 0, st>>>(n, k0, OZ_B, 0, Z, mask);
+        k_oz_slice_S<<<dim3(n / 64, W), 256, 0, st>>>(n, k0, OZ_B, 0, 0, Z, mask);
+        const OzCols outer{0, n, k0, k0 + OZ_B, 0, n / OZ_TJ};
+        k_oz_gemm<OZ_B / 16><<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, outer, Z, mask, err);
         if (hook) hook(hctx, 5, 0);
     }
     launch_oz_finish(W, n, Z, S, mask, delayed, reset_tau, st);
@@ -486,7 +510,8 @@ bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, co
         case 4: kern = k_oz_gemm<4>; break;
         default: break;
     }
-    kern<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, n, Z, Z.go, err);
+    const OzCols all{0, n, -1, -1, 0, n / OZ_TJ};
+    kern<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, all, Z, Z.go, err);
     return true;
 }
 
