@@ -215,11 +215,14 @@ def run_arm(L, torch, args, arm, Phi_d, occ0, slot_d, new_d, rank, world, dist):
 
 def refresh_roofline(prof, n, W, bf16_sustained):
     """Rooflines of the refresh.  Tensor-core form (panel / update classes
-    timed): the FP64 panel eliminations do n * 64^2 FMA per panel, 2 * 64 n^2
-    flop per walker, on the FP64 pipe; the split-product updates execute
-    28 BF16 MMA products of n x n x 64 per panel, 56 n^3 flop per walker, on
-    the tensor pipe (their FP64-equivalent work is 2 n^2 (n - 64) flop).  The
-    FP64 Gauss-Jordan form does n^3 FMA = 2 n^3 flop per walker."""
+    timed): a panel's work is n * 64^2 FMA, 2 * 64 n^2 flop per walker per
+    refresh, done as FP64 eliminations of 16-column sub-panels plus their
+    K = 16 split-product updates of the other panel columns; it is reported
+    as FP64-equivalent throughput against the FP64 pipe.  The full-width
+    split-product updates execute 39 BF16 MMA products of n x n x 64 per panel,
+    78 n^3 flop per walker, on the tensor pipe (FP64-equivalent work
+    2 n^2 (n - 64) flop).  The FP64 Gauss-Jordan form does n^3 FMA = 2 n^3 flop
+    per walker."""
     ms, cnt = prof["refresh"]
     if not cnt:
         return None
@@ -230,9 +233,10 @@ def refresh_roofline(prof, n, W, bf16_sustained):
     if pcnt and ucnt:
         p_ms, u_ms = pms / cnt, ums / cnt          # per refresh
         p_flop = 2.0 * 64 * n * n * W
-        u_flop = 56.0 * n ** 3 * W
+        u_flop = 78.0 * n ** 3 * W
         u_eq = 2.0 * n * n * (n - 64) * W
-        panel = {"kernel": "refresh panel eliminations (FP64)", "bound": "alu", "unit": "TFLOP/s",
+        panel = {"kernel": "refresh panels (FP64 sub-panel eliminations + split-product inner updates; "
+                           "FP64-equivalent)", "bound": "alu", "unit": "TFLOP/s",
                  "achieved": p_flop / (p_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                  "frac": p_flop / (p_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
                  "flop_per_refresh": p_flop, "ms_per_refresh": p_ms, "peak_source": fp64_src}
