@@ -179,11 +179,12 @@ __device__ __forceinline__ double oz_i64_to_double(long long F, int e) {
     return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
-// Trailing update of panel k0 (nks K-steps of 16: 4 for a 64-column panel).
-// Persistent CTAs take (walker, 128-column
-// block) units: the 7 S slices of the block are loaded once, then the 64-row
-// tiles i stream through; the Pan slices of tile i+1 are loaded (TMA) while
-// the epilogue of tile i runs.  Columns of the panel itself are left alone.
+// M[i][j] += 2^(E_i + E_j) sum_c Pan[i][c] S[c][j] as a split product, with
+// NKS K-steps of 16 (4 for a 64-column panel, 1 for a sub-panel or the K = 16
+// flush), written only for the columns cols selects.  Persistent CTAs take
+// (walker, 128-column block) units: the 7 S slices of the block are loaded
+// once, then the 64-row tiles i stream through; the Pan slices of tile i+1
+// are loaded (TMA) while the epilogue of tile i runs.
 constexpr int OZ_THREADS = 512;   // 16 warps: 4 per TMEM lane quarter, each 16 of the 64 rows i
 
 template <int NKS>
