@@ -7,7 +7,12 @@ walkers, each a Slater matrix A = Phi[occ] with Phi 2048 x 1024 N(0, 1/n)
 V = Phi[new] - Phi[old]) accepted every step, and a from-scratch FP64 refresh
 of every walker after every 128th step.  One step = operand formation +
 propose + accept (+ flush) for all walkers.  Metric: walker-updates/s, for the
-delayed form (K = 16, flush on the tensor cores) and the plain FP64 form.
+delayed form (K = 16, FP64 GEMV, flush as an exact split product on the
+tensor cores; the headline "delayed" arm) and the plain FP64 form, with the
+double-float, 3xTF32 and double-float-GEMV delayed forms as further arms.
+The line's roofline is that of the kernel class with the most time (the
+accept, on the FP64 pipe); the refresh's FP64 panels and tensor-core updates
+are reported beside it.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank runs its own W walkers (weak scaling); rank 0
