@@ -14,7 +14,13 @@ The line's roofline is that of the kernel class with the most time (the
 accept, on the FP64 pipe); the refresh's FP64 panels and tensor-core updates
 are reported beside it.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+`--workload pf` times the Pfaffian form instead (Sec. 3): W = 1024 walkers,
+n = 256 particles on 512 sites, A = F[pos][:, pos] with F = G - G^T and G
+512 x 512 N(0, 1/n), rank-2 row-and-column moves (B = [x, e_i], C = -J), the
+plain FP64 form against the delayed form (K = 8) with an FP64 or a
+double-float skew flush, no refresh.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload det|pf]
 Under torchrun every rank runs its own W walkers (weak scaling); rank 0
 prints one JSON line.
 """
@@ -47,17 +53,31 @@ def parse():
     p.add_argument("--steps", type=int, default=256)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--walkers", type=int, default=1024)
-    p.add_argument("--n", type=int, default=1024)
-    p.add_argument("--m", type=int, default=2048)
-    p.add_argument("--delay", type=int, default=16)
-    p.add_argument("--refresh-every", type=int, default=128)
-    p.add_argument("--arms", default="plain,delayed,delayed_dfflush,delayed_tf32x3,delayed_dfgemv",
-                   help="comma list of " + ",".join(ARMS))
+    p.add_argument("--workload", default="det", choices=["det", "pf"])
+    p.add_argument("--walkers", type=int, default=None)
+    p.add_argument("--n", type=int, default=None)
+    p.add_argument("--m", type=int, default=None)
+    p.add_argument("--delay", type=int, default=None)
+    p.add_argument("--refresh-every", type=int, default=None, help="0: no refresh")
+    p.add_argument("--arms", default=None,
+                   help="comma list of " + ",".join(ARMS) + " (det) or " + ",".join(PF_ARMS) + " (pf)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--seed", type=int, default=6)
-    return p.parse_args()
+    a = p.parse_args()
+    for key, val in DEFAULTS[a.workload].items():
+        if getattr(a, key) is None:
+            setattr(a, key, val)
+    return a
+
+
+# walkers, n, sites m, delay K, refresh period and arms of each workload
+DEFAULTS = {
+    "det": {"walkers": 1024, "n": 1024, "m": 2048, "delay": 16, "refresh_every": 128,
+            "arms": "plain,delayed,delayed_dfflush,delayed_tf32x3,delayed_dfgemv"},
+    "pf": {"walkers": 1024, "n": 256, "m": 512, "delay": 8, "refresh_every": 0,
+           "arms": "plain,delayed,delayed_dfflush"},
+}
 
 
 # --------------------------------------------------------------------------
@@ -116,6 +136,15 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # the oracle on the host cores (CPU baseline and the reference arm)
 # --------------------------------------------------------------------------
+def host_threads():
+    """Threads the oracle's BLAS/LAPACK calls use on the host cores."""
+    try:
+        import threadpoolctl
+        return int(max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or 1)
+    except Exception:
+        return int(os.cpu_count() or 1)
+
+
 def cpu_baseline(Phi, occ0, slot, new, n, budget_s=15.0):
     from oracle import lru_oracle as O
     steps = min(32, slot.shape[0])
@@ -133,12 +162,7 @@ def cpu_baseline(Phi, occ0, slot, new, n, budget_s=15.0):
         wl += 1
         if tsum > budget_s:
             break
-    try:
-        import threadpoolctl
-        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or 1
-    except Exception:
-        cores = os.cpu_count() or 1
-    return {"value": done / tsum, "unit": "walker-updates/s", "cores": int(cores), "kind": "oracle",
+    return {"value": done / tsum, "unit": "walker-updates/s", "cores": host_threads(), "kind": "oracle",
             "sample": f"plain FP64 chain (oracle det_lru, Eq. det_inv) of {wl} walkers x {steps} steps at n={n}, "
                       f"{tsum:.1f} s"}
 
@@ -182,10 +206,21 @@ def run_arm(L, torch, args, arm, Phi_d, occ0, slot_d, new_d, rank, world, dist):
         st.propose_det(U_op, V_op, ratio if timed_idx is None else ratios_all[timed_idx], status)
         st.accept()
         st.commit_moves(occ_d, slot_d[s], new_d[s])
-        if timed_idx is not None and (timed_idx + 1) % args.refresh_every == 0:
+        if timed_idx is not None and args.refresh_every and (timed_idx + 1) % args.refresh_every == 0:
             st.gather_rows(Phi_d, occ_d, A)
             st.refresh(A, want_drift=False)
 
+    ms, clk, launches, prof = timed_steps(torch, st, step, args, dist, dev)
+    tau = st.tau().cpu().numpy() if delayed else None
+    st.close()
+    return ratios_all, ms, clk, launches, prof, tau, (delay, arith, flush)
+
+
+def timed_steps(torch, st, step, args, dist, dev):
+    """W warm-up steps, then K steps between CUDA events on the launching
+    stream (barrier + synchronize on both sides, clocks sampled meanwhile,
+    max over ranks); the library's per-class kernel timers run over the same
+    region."""
     for s in range(args.warmup):
         step(s, None)
     torch.cuda.synchronize()
@@ -213,9 +248,7 @@ def run_arm(L, torch, args, arm, Phi_d, occ0, slot_d, new_d, rank, world, dist):
     prof = {name: st.profile_read(c) for c, name in enumerate(PROF_CLASSES)}
     st.profile(False)
     ms = multigpu.max_over_ranks(ms, dist, "cuda")
-    tau = st.tau().cpu().numpy() if delayed else None
-    st.close()
-    return ratios_all, ms, clk, launches, prof, tau, (delay, arith, flush)
+    return ms, clk, launches, prof
 
 
 def refresh_roofline(prof, n, W, bf16_sustained):
@@ -267,7 +300,7 @@ def refresh_roofline(prof, n, W, bf16_sustained):
 ACCEPT_DELAYED_TRAFFIC_PER_WALKER_N1024 = (545.827584e6 + 4.03712e6) / 64
 
 
-def accept_roofline(delay, arith, n, W, ms, hbm):
+def accept_roofline(delay, arith, n, W, ms, hbm, pf=False):
     """Roofline of one accept launch (one walker-update of every walker).
 
     Algorithmic bytes: plain reads and writes A^{-1} (2 n^2 x 8 B per walker);
@@ -275,14 +308,19 @@ def accept_roofline(delay, arith, n, W, ms, hbm):
     plain n^2 FMA for y = V A^{-1} plus n^2 for the rank-1 update, delayed
     n^2 FMA.  The bound is whichever takes longer at its peak (HBM copy
     bandwidth, FP64 pipe); the double-float GEMV runs on the FP32 pipe and is
-    reported against HBM.
+    reported against HBM.  Pfaffian row-and-column move (B = [x, e_i]): plain
+    does n^2 FMA for x^T A^{-1} (the e_i column is a read) plus 2 n^2 for the
+    rank-2 update; delayed does the n^2 FMA GEMV only.
     """
     bytes_per = (2 if delay < 2 else 1) * n * n * 8 * W
-    flop_per = (4 if delay < 2 else 2) * n * n * W
+    if pf:
+        flop_per = (6 if delay < 2 else 2) * n * n * W
+    else:
+        flop_per = (4 if delay < 2 else 2) * n * n * W
     t_hbm = bytes_per / (hbm * 1e9)
     t_fp64 = flop_per / (FP64_PEAK_TFLOPS * 1e12)
-    traffic = ACCEPT_DELAYED_TRAFFIC_PER_WALKER_N1024 * W if (delay >= 2 and arith == "native" and n == 1024) \
-        else None
+    traffic = ACCEPT_DELAYED_TRAFFIC_PER_WALKER_N1024 * W if (
+        not pf and delay >= 2 and arith == "native" and n == 1024) else None
     out = {"bytes_per_launch": bytes_per, "fp64_flop_per_launch": flop_per if arith == "native" else 0,
            "ms_per_launch": ms, "traffic": traffic,
            "hbm": {"achieved": bytes_per / (ms / 1e3) / 1e9 if ms else None, "peak": hbm, "unit": "GB/s"},
@@ -331,7 +369,7 @@ def e2e_arm(L, torch, args, Phi_d, occ0, slot_h, new_h, steps):
         st.accept()
         st.commit_moves(occ_d, sl_d, nw_d)
         r_h[s].copy_(ratio, non_blocking=True)
-        if (s + 1) % args.refresh_every == 0:
+        if args.refresh_every and (s + 1) % args.refresh_every == 0:
             st.gather_rows(Phi_d, occ_d, A)
             st.refresh(A, want_drift=False)
     e1.record()
@@ -368,12 +406,269 @@ def exact_parity(Phi, occ0, slot, new, ratios, walkers, steps):
             "median_rel": float(np.median(out)), "p99_rel": float(np.quantile(out, 0.99))}
 
 
+def drift_vs_plain(arm_ratios, arms):
+    """Drift of every arm's ratios against the plain FP64 arm (same moves);
+    steps within 1e-6 of the median |ratio| (near a node) are counted apart."""
+    if "plain" not in arm_ratios:
+        return
+    ref = arm_ratios["plain"]
+    med = ref.abs().median()
+    gate = ref.abs() >= 1e-6 * med
+    for arm, r in arm_ratios.items():
+        if arm == "plain":
+            continue
+        d = (r - ref).abs()
+        relerr = (d / ref.abs())[gate]
+        arms[arm]["ratio_err_vs_plain_fp64"] = {
+            "max_rel": relerr.max().item(), "median_rel": relerr.median().item(),
+            "p999_rel": relerr.float().quantile(0.999).item() if relerr.numel() < 16_000_000 else None,
+            "max_abs_over_median_abs": (d.max() / med).item(), "near_node_steps": int((~gate).sum().item())}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
     return 6800.0, 1700.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# Pfaffian workload (Sec. 3): rank-2 row-and-column moves
+# --------------------------------------------------------------------------
+# name -> (delay, flush): plain FP64 Woodbury step (Eq. pf_inv), delayed form
+# (Sec. 3.3) with the skew FP64 flush or the double-float skew flush
+PF_ARMS = {
+    "plain": (0, "native"),
+    "delayed": (None, "native"),
+    "delayed_dfflush": (None, "df"),
+}
+PF_METRIC = "walker-updates/sec, Pfaffian rank-2 row-and-column moves (delayed vs plain, same GPU); roofline fraction"
+
+
+def pf_inputs(args, rank):
+    """F = G - G^T (G m x m, N(0, 1/n)), initial positions and the move
+    sequence of the Pfaffian workload, seeded per rank."""
+    from paper_2602_05255_gb300 import workloads
+    seed = multigpu.shard_seed(args.seed, rank)
+    G = workloads.pairing_generator(seed, args.m, 1.0 / args.n)
+    F = G - G.T
+    pos0 = workloads.initial_occupation(seed + 1, args.walkers, args.m, args.n)
+    slot, new = workloads.move_sequence(seed + 2, pos0, args.m, args.warmup + args.steps)
+    return F, pos0, slot, new
+
+
+def pf_workload_name(args):
+    return (f"pf rank-2 row+column moves, W={args.walkers} walkers/GPU, n={args.n} on {args.m} sites, "
+            f"F = G - G^T with G N(0,1/n) FP64, K={args.delay}, "
+            + (f"refresh every {args.refresh_every}" if args.refresh_every else "no refresh"))
+
+
+def pf_state(L, torch, args, delay, flush, F_d, pos0):
+    """A Pfaffian handle initialised from F[pos][:, pos], with its move buffers."""
+    W, n = args.walkers, args.n
+    st = L.LowRankState("pf", W, n, k=1, dtype=torch.float64, delay=delay, flush=FLUSH[flush])
+    pos_d = torch.tensor(pos0, device="cuda")
+    A = st.gather_pairs(F_d, pos_d)
+    st.init(A)
+    B = torch.empty(W, 2, n, dtype=torch.float64, device="cuda")
+    idx = torch.empty(W, 2, dtype=torch.int32, device="cuda")
+    B_op = L.Operand(dense=B, idx=idx, onehot_mask=0b10)     # B = [x, e_i], C = -J
+    return st, pos_d, A, B, idx, B_op
+
+
+def run_pf_arm(L, torch, args, arm, F_d, pos0, slot_d, new_d, dist):
+    W = args.walkers
+    dev = torch.cuda.current_device()
+    delay, flush = PF_ARMS[arm]
+    delay = args.delay if delay is None else delay
+    st, pos_d, A, B, idx, B_op = pf_state(L, torch, args, delay, flush, F_d, pos0)
+    ratio = torch.empty(W, dtype=torch.float64, device="cuda")
+    ratios_all = torch.empty(args.steps, W, dtype=torch.float64, device="cuda")
+    status = torch.empty(W, dtype=torch.int32, device="cuda")
+
+    def step(s, timed_idx):
+        st.form_pf_moves(F_d, pos_d, slot_d[s], new_d[s], B, idx)
+        st.propose_pf(B_op, None, ratio if timed_idx is None else ratios_all[timed_idx], status)
+        st.accept()
+        st.commit_moves(pos_d, slot_d[s], new_d[s])
+        if timed_idx is not None and args.refresh_every and (timed_idx + 1) % args.refresh_every == 0:
+            st.gather_pairs(F_d, pos_d, A)
+            st.refresh(A, want_drift=False)
+
+    ms, clk, launches, prof = timed_steps(torch, st, step, args, dist, dev)
+    st.close()
+    return ratios_all, ms, clk, launches, prof, (delay, flush)
+
+
+def pf_flush_roofline(flush, n, W, K, ms_per_full, hbm):
+    """One full skew flush of every walker: A_0^{-1} += P Q^T over K steps of
+    2 slot columns (Eq. pf_delayed_Ainv), the upper half computed and
+    mirrored, n (n + 1) / 2 x 2K FMA per walker, reading and writing
+    A_0^{-1} once (2 n^2 x 8 B).  The FP64 flush is bound by the FP64 pipe;
+    the double-float flush runs on the FP32 pipe and is reported against HBM
+    with its FP64-equivalent rate."""
+    if not ms_per_full:
+        return None
+    flop = 2.0 * (n * (n + 1) / 2) * 2 * K * W
+    byt = 2.0 * n * n * 8 * W
+    out = {"flop_per_full_flush": flop, "bytes_per_full_flush": byt, "ms_per_full_flush": ms_per_full,
+           "fp64_equivalent_tflops": flop / (ms_per_full / 1e3) / 1e12,
+           "hbm": {"achieved": byt / (ms_per_full / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"}}
+    out["hbm"]["frac"] = out["hbm"]["achieved"] / hbm
+    if flush == "native":
+        out.update({"bound": "alu", "achieved": out["fp64_equivalent_tflops"], "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": out["fp64_equivalent_tflops"] / FP64_PEAK_TFLOPS})
+    else:
+        out.update({"bound": "hbm", "achieved": out["hbm"]["achieved"], "peak": hbm, "unit": "GB/s",
+                    "frac": out["hbm"]["frac"]})
+    return out
+
+
+def exact_parity_pf(F, pos0, slot, new, ratios, walkers, steps):
+    """Relative error of |r| for sampled walkers against the exact
+    |pf A' / pf A| = exp((log|det A'| - log|det A|) / 2) (pf^2 = det; LAPACK
+    slogdet on the host).  The sign is compared through the drift against
+    the plain FP64 arm."""
+    out = []
+    for w in walkers:
+        pos = pos0[w].copy()
+        for s in range(steps):
+            A0 = F[np.ix_(pos, pos)]
+            pos[slot[s, w]] = new[s, w]
+            A1 = F[np.ix_(pos, pos)]
+            mag = math.exp((np.linalg.slogdet(A1)[1] - np.linalg.slogdet(A0)[1]) / 2)
+            out.append(abs(abs(ratios[s, w]) - mag) / mag)
+    out = np.array(out)
+    return {"walkers": list(walkers), "steps": steps, "of": "|ratio|", "max_rel": float(out.max()),
+            "median_rel": float(np.median(out)), "p99_rel": float(np.quantile(out, 0.99))}
+
+
+def cpu_baseline_pf(F, pos0, slot, new, n, budget_s=15.0):
+    from oracle import lru_oracle as O
+    steps = min(32, slot.shape[0])
+    done, tsum, wl = 0, 0.0, 0
+    for w in range(pos0.shape[0]):
+        pos = pos0[w].copy()
+        Ainv = np.linalg.inv(O.pairing_matrix(F, pos))
+        ts = time.perf_counter()
+        for s in range(steps):
+            B, C = O.pf_row_col_move(F, pos, slot[s, w], new[s, w])
+            r, Ainv = O.pf_lru(Ainv, B, C, return_update=True)
+            pos[slot[s, w]] = new[s, w]
+        tsum += time.perf_counter() - ts
+        done += steps
+        wl += 1
+        if tsum > budget_s:
+            break
+    return {"value": done / tsum, "unit": "walker-updates/s", "cores": host_threads(), "kind": "oracle",
+            "sample": f"plain FP64 Pfaffian chain (oracle pf_lru, Eq. pf_inv) of {wl} walkers x {steps} steps "
+                      f"at n={n}, {tsum:.1f} s"}
+
+
+def e2e_pf_arm(L, torch, args, F_d, pos0, slot_h, new_h, steps):
+    """The Pfaffian metric through the C-ABI with host buffers: each step
+    copies its moves host->device from pinned memory and reads the ratios
+    back inside the timed region (delayed form, FP64 skew flush)."""
+    W = args.walkers
+    st, pos_d, A, B, idx, B_op = pf_state(L, torch, args, args.delay, "native", F_d, pos0)
+    ratio = torch.empty(W, dtype=torch.float64, device="cuda")
+    status = torch.empty(W, dtype=torch.int32, device="cuda")
+    sl_h = torch.from_numpy(np.ascontiguousarray(slot_h)).pin_memory()
+    nw_h = torch.from_numpy(np.ascontiguousarray(new_h)).pin_memory()
+    r_h = torch.empty(steps, W, dtype=torch.float64).pin_memory()
+    sl_d = torch.empty(W, dtype=torch.int32, device="cuda")
+    nw_d = torch.empty(W, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in range(steps):
+        sl_d.copy_(sl_h[s], non_blocking=True)
+        nw_d.copy_(nw_h[s], non_blocking=True)
+        st.form_pf_moves(F_d, pos_d, sl_d, nw_d, B, idx)
+        st.propose_pf(B_op, None, ratio, status)
+        st.accept()
+        st.commit_moves(pos_d, sl_d, nw_d)
+        r_h[s].copy_(ratio, non_blocking=True)
+        if args.refresh_every and (s + 1) % args.refresh_every == 0:
+            st.gather_pairs(F_d, pos_d, A)
+            st.refresh(A, want_drift=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st.close()
+    return {"value": W * steps / (ms / 1e3), "unit": "walker-updates/s",
+            "h2d_bytes_per_step": 2 * W * 4, "d2h_bytes_per_step": W * 8, "steps": steps}
+
+
+def main_pf(args, torch, L, rank, world, dist):
+    W, n = args.walkers, args.n
+    F, pos0, slot, new = pf_inputs(args, rank)
+    F_d = torch.tensor(F, device="cuda")
+    slot_d = torch.tensor(slot, device="cuda")
+    new_d = torch.tensor(new, device="cuda")
+    hbm, _, peak_src = load_peaks()
+    arms, arm_ratios = {}, {}
+    order = [a.strip() for a in args.arms.split(",") if a.strip()]
+    for arm in order:
+        ratios_all, ms, clk, launches, prof, (delay, flush) = run_pf_arm(
+            L, torch, args, arm, F_d, pos0, slot_d, new_d, dist)
+        arm_ratios[arm] = ratios_all
+        acc_ms, acc_n = prof["accept"]
+        a = {"value": multigpu.whole_job_rate(W * args.steps, world, ms), "ms_per_step": ms / args.steps,
+             "delay_K": delay, "flush": flush if delay >= 2 else None,
+             "kernel_ms": {k: v[0] for k, v in prof.items()},
+             "kernel_launches_timed": {k: v[1] for k, v in prof.items()},
+             "gpu_launches": launches, "clocks": clk,
+             "accept_roofline": accept_roofline(delay, "native", n, W, acc_ms / acc_n if acc_n else None, hbm,
+                                                pf=True)}
+        if delay >= 2:
+            nfl = args.steps // delay
+            a["flush_roofline"] = pf_flush_roofline(flush, n, W, delay, prof["flush"][0] / nfl if nfl else None, hbm)
+        arms[arm] = a
+    drift_vs_plain(arm_ratios, arms)
+    if rank == 0:
+        psteps = min(args.steps, 64)
+        pos_t = pos0.copy()                      # positions at the start of the timed region
+        for s_ in range(args.warmup):
+            pos_t[np.arange(W), slot[s_]] = new[s_]
+        for arm, r in arm_ratios.items():
+            arms[arm]["parity_vs_exact"] = exact_parity_pf(
+                F, pos_t, slot[args.warmup:], new[args.warmup:], r[:psteps].cpu().numpy(), [0, W // 2], psteps)
+    main_arm = "delayed" if "delayed" in arms else order[0]
+    head = arms[main_arm]
+    km = head["kernel_ms"]
+    # the line's roofline belongs to the kernel class that takes the most time
+    cand = {"accept": (km.get("accept", 0.0), head["accept_roofline"])}
+    if head.get("flush_roofline"):
+        cand["flush"] = (km.get("flush", 0.0), head["flush_roofline"])
+    dom = max(cand, key=lambda k: cand[k][0])
+    roof = dict(cand[dom][1])
+    roof["kernel"] = dom
+    roof["dominant_kernel_by_time"] = dom
+    roof["kernel_ms_in_timed_region"] = {k: v[0] for k, v in cand.items()}
+    roof["peak_source"] = ("derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz" if roof["bound"] == "alu"
+                           else ("HBM of measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                                 else "HBM of fallback"))
+    line = {
+        "metric": PF_METRIC, "value": head["value"], "unit": "walker-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": pf_workload_name(args), "arm": main_arm, "delay_K": args.delay,
+                   "walkers_per_gpu": W, "n": n, "m": args.m,
+                   "l2": f"inputs larger than L2 (A^{{-1}} state {W * n * n * 8 / 2**20:.0f} MiB per GPU)"},
+        "roofline": roof, "arms": arms, "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+    }
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e_pf_arm(L, torch, args, F_d, pos0, slot[args.warmup:], new[args.warmup:], args.steps)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_pf(F, pos0, slot, new, n)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
 
 
 def main():
@@ -393,6 +688,8 @@ def main():
     torch.cuda.set_device(local)
     from paper_2602_05255_gb300 import lrugb as L
     from paper_2602_05255_gb300 import workloads
+    if args.workload == "pf":
+        return main_pf(args, torch, L, rank, world, dist)
 
     W, n, m = args.walkers, args.n, args.m
     seed = multigpu.shard_seed(args.seed, rank)
@@ -417,7 +714,7 @@ def main():
         a = {"value": multigpu.whole_job_rate(W * args.steps, world, ms), "ms_per_step": ms / args.steps,
              "delay_K": delay, "gemv_arith": arith, "flush": flush if delay >= 2 else None,
              "value_excl_refresh": upd / ((ms - ref_ms) / 1e3) if ms > ref_ms else None,
-             "refreshes_in_timed_region": args.steps // args.refresh_every, "refresh_ms_total": ref_ms,
+             "refreshes_in_timed_region": args.steps // args.refresh_every if args.refresh_every else 0, "refresh_ms_total": ref_ms,
              "kernel_ms": {k: v[0] for k, v in prof.items()},
              "kernel_launches_timed": {k: v[1] for k, v in prof.items()},
              "gpu_launches": launches, "clocks": clk, "_prof": prof}
@@ -430,20 +727,7 @@ def main():
                                  "ms_per_full_flush": fl_ms / max(nfl, 1),
                                  "bytes_per_full_flush": 2 * n * n * 8 * W}
         arms[arm] = a
-    # drift of every arm's ratios against the plain FP64 arm (same moves)
-    if "plain" in arm_ratios:
-        ref = arm_ratios["plain"]
-        med = ref.abs().median()
-        gate = ref.abs() >= 1e-6 * med
-        for arm, r in arm_ratios.items():
-            if arm == "plain":
-                continue
-            d = (r - ref).abs()
-            relerr = (d / ref.abs())[gate]
-            arms[arm]["ratio_err_vs_plain_fp64"] = {
-                "max_rel": relerr.max().item(), "median_rel": relerr.median().item(),
-                "p999_rel": relerr.float().quantile(0.999).item() if relerr.numel() < 16_000_000 else None,
-                "max_abs_over_median_abs": (d.max() / med).item(), "near_node_steps": int((~gate).sum().item())}
+    drift_vs_plain(arm_ratios, arms)
     # exact parity of two sampled walkers (the first 64 timed steps)
     if rank == 0:
         psteps = min(args.steps, 64)
@@ -480,8 +764,7 @@ def main():
         "metric": METRIC, "value": head["value"], "unit": "walker-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"det rank-1 row moves, W={W} walkers/GPU, n={n}, Phi {m}x{n} N(0,1/n) FP64, "
-                               f"refresh every {args.refresh_every}", "arm": main_arm,
+        "config": {"workload": det_workload_name(args), "arm": main_arm,
                    "delay_K": args.delay, "walkers_per_gpu": W, "n": n, "m": m,
                    "l2": "inputs larger than L2 (A^{-1} state 8 GiB per GPU)"},
         "roofline": roof, "roofline_accept": acc_roof, "roofline_refresh": ref_roof,
@@ -501,21 +784,38 @@ def main():
     return 0
 
 
+def det_workload_name(args):
+    return (f"det rank-1 row moves, W={args.walkers} walkers/GPU, n={args.n}, Phi {args.m}x{args.n} N(0,1/n) FP64, "
+            + (f"refresh every {args.refresh_every}" if args.refresh_every else "no refresh"))
+
+
 def reference_arm(args):
-    """The oracle as it stands on the host cores (there is no reference code)."""
+    """The oracle as it stands on the host cores (there is no reference code),
+    on a bounded sample of the same workload: the plain FP64 chain of as many
+    walkers as fit the time budget, each for up to 16 steps."""
     from paper_2602_05255_gb300 import workloads
     W, n, m = args.walkers, args.n, args.m
-    Phi = workloads.orbital_matrix(args.seed, m, n, 1.0 / n)
-    occ0 = workloads.initial_occupation(args.seed + 1, W, m, n)
-    slot, new = workloads.move_sequence(args.seed + 2, occ0, m, max(4, min(args.steps, 16)))
+    budget = max(5.0, min(60.0, 2.0 * args.steps))
+    nsteps = max(4, min(args.steps, 16))
     t0 = time.perf_counter()
-    cb = cpu_baseline(Phi, occ0, slot, new, n, budget_s=max(5.0, min(60.0, 2.0 * args.steps)))
+    if args.workload == "pf":
+        sample = argparse.Namespace(**vars(args))
+        sample.warmup, sample.steps = 0, nsteps
+        F, pos0, slot, new = pf_inputs(sample, 0)
+        cb = cpu_baseline_pf(F, pos0, slot, new, n, budget_s=budget)
+        metric, name = PF_METRIC, pf_workload_name(args)
+    else:
+        Phi = workloads.orbital_matrix(args.seed, m, n, 1.0 / n)
+        occ0 = workloads.initial_occupation(args.seed + 1, W, m, n)
+        slot, new = workloads.move_sequence(args.seed + 2, occ0, m, nsteps)
+        cb = cpu_baseline(Phi, occ0, slot, new, n, budget_s=budget)
+        metric, name = METRIC, det_workload_name(args)
     el = time.perf_counter() - t0
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "walker-updates/s",
+    line = {"impl": "reference", "metric": metric, "value": cb["value"], "unit": "walker-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * W / cb["value"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"det rank-1 row moves, W={W}, n={n}, Phi {m}x{n} N(0,1/n) FP64 (oracle sample)"},
+            "config": {"workload": name},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "walker-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": el}
