@@ -216,6 +216,21 @@ __device__ void propose_walker(const int w, const DevLayout L, const DevState<T>
         int dl[MAXKK], nd = 0;
         for (int a = 0; a < kk; ++a)
             if (s_iu[a] < 0) dl[nd++] = a;
+        if (nd == 1) {
+            // one dense column (the Pfaffian row-and-column move, a rank-1
+            // dense update): each thread walks the columns for its rows with
+            // the loads of eight columns in flight, one accumulator per row
+            // (the same FMA order as the grouped loop below)
+            const T* u0 = vec_ptr<T>(U, L, w, dl[0], n);
+            T* Xa = X + (long long)dl[0] * n;
+            for (int j = tid; j < n; j += PT) {
+                T acc = s_zero(T());
+#pragma unroll 8
+                for (int l = 0; l < n; ++l) acc = s_fma(G[(long long)l * n + j], u0[l], acc);
+                Xa[j] = acc;
+            }
+            nd = 0;
+        }
         for (int g0 = 0; g0 < nd; g0 += 4) {
             const int ng = min(4, nd - g0);
             T acc[4][JPT];
