@@ -106,6 +106,30 @@ struct TileIter {
     }
 };
 
+// Walkers due for a flush, read a chunk at a time into shared memory (one
+// coalesced read of tau per chunk) rather than by one dependent load per
+// walker in every CTA, so that a step with no walker due costs a short scan.
+// s_tau[i] = tau of walker w0 + i if it is due, else -1; returns the chunk
+// length.  Called by every thread of a FLUSH_SCAN-thread CTA.
+constexpr int FLUSH_SCAN = 256;
+
+template <typename T>
+__device__ __forceinline__ int flush_scan(const DevLayout& L, const DevState<T>& S, const uint8_t* force, int w0,
+                                          int* s_tau) {
+    __syncthreads();   // the previous chunk's readers are done
+    const int w = w0 + (int)threadIdx.x;
+    if (threadIdx.x < FLUSH_SCAN) {
+        int t = -1;
+        if (w < L.W) {
+            const int tau = S.tau[w];
+            if (force ? (force[w] && tau > 0) : (tau >= L.K)) t = tau;
+        }
+        s_tau[threadIdx.x] = t;
+    }
+    __syncthreads();
+    return min(FLUSH_SCAN, L.W - w0);
+}
+
 // ---------------------------------------------------------------------------
 // propose: X = A^{-1} U (delayed: A_0^{-1} U -/+ P (Q^T U)), core, small solve
 // det: Sec. 2.1 Eq. det_R, delayed Sec. 2.3 (R_tau, a_tau equations)
@@ -795,17 +819,21 @@ __device__ void flush_df_tile(const DevLayout& L, const DevState<double>& S, int
 template <bool PF>
 __global__ void __launch_bounds__(256) k_flush_df(DevLayout L, DevState<double> S, const uint8_t* force) {
     __shared__ DfFlushSmem sm;
+    __shared__ int s_tau[FLUSH_SCAN];
     TileIter ti;
-    for (int w = 0; w < L.W; ++w) {
-        const int tau = S.tau[w];
-        const bool go = force ? (force[w] && tau > 0) : (tau >= L.K);
-        if (!go) continue;
-        const int nt = (L.nw(w) + 31) / 32;
-        const int ntl = TileIter::tiles(nt, PF);
-        for (long long t = ti.first(ntl); t < ntl; t += gridDim.x) {
-            int tJ, tL;
-            TileIter::coords(t, nt, PF, tJ, tL);
-            flush_df_tile<PF>(L, S, w, tau, tJ, tL, sm);
+    for (int w0 = 0; w0 < L.W; w0 += FLUSH_SCAN) {
+        const int wn = flush_scan(L, S, force, w0, s_tau);
+        for (int i = 0; i < wn; ++i) {
+            const int tau = s_tau[i];
+            if (tau < 0) continue;
+            const int w = w0 + i;
+            const int nt = (L.nw(w) + 31) / 32;
+            const int ntl = TileIter::tiles(nt, PF);
+            for (long long t = ti.first(ntl); t < ntl; t += gridDim.x) {
+                int tJ, tL;
+                TileIter::coords(t, nt, PF, tJ, tL);
+                flush_df_tile<PF>(L, S, w, tau, tJ, tL, sm);
+            }
         }
     }
 }
@@ -1012,17 +1040,21 @@ __global__ void __launch_bounds__(256) k_flush_native(DevLayout L, DevState<T> S
     __shared__ T sP[32][65];
     __shared__ T sQ[32][65];
     __shared__ T sT[32][33];
+    __shared__ int s_tau[FLUSH_SCAN];
     TileIter ti;
-    for (int w = 0; w < L.W; ++w) {
-        const int tau = S.tau[w];
-        const bool go = force ? (force[w] && tau > 0) : (tau >= L.K);
-        if (!go) continue;
-        const int nt = (L.nw(w) + 31) / 32;
-        const int ntl = TileIter::tiles(nt, PF);
-        for (long long t = ti.first(ntl); t < ntl; t += gridDim.x) {
-            int tJ, tL;
-            TileIter::coords(t, nt, PF, tJ, tL);
-            flush_native_tile<T, PF>(L, S, w, tau, tJ, tL, sP, sQ, sT);
+    for (int w0 = 0; w0 < L.W; w0 += FLUSH_SCAN) {
+        const int wn = flush_scan(L, S, force, w0, s_tau);
+        for (int i = 0; i < wn; ++i) {
+            const int tau = s_tau[i];
+            if (tau < 0) continue;
+            const int w = w0 + i;
+            const int nt = (L.nw(w) + 31) / 32;
+            const int ntl = TileIter::tiles(nt, PF);
+            for (long long t = ti.first(ntl); t < ntl; t += gridDim.x) {
+                int tJ, tL;
+                TileIter::coords(t, nt, PF, tJ, tL);
+                flush_native_tile<T, PF>(L, S, w, tau, tJ, tL, sP, sQ, sT);
+            }
         }
     }
 }
