@@ -308,9 +308,10 @@ def accept_roofline(delay, arith, n, W, ms, hbm, pf=False):
     plain n^2 FMA for y = V A^{-1} plus n^2 for the rank-1 update, delayed
     n^2 FMA.  The bound is whichever takes longer at its peak (HBM copy
     bandwidth, FP64 pipe); the double-float GEMV runs on the FP32 pipe and is
-    reported against HBM.  Pfaffian row-and-column move (B = [x, e_i]): plain
-    does n^2 FMA for x^T A^{-1} (the e_i column is a read) plus 2 n^2 for the
-    rank-2 update; delayed does the n^2 FMA GEMV only.
+    reported against HBM.  Pfaffian row-and-column move (B = [x, e_i]), plain
+    form: n^2 FMA for x^T A^{-1} (the e_i column is a read) plus 2 n^2 for the
+    rank-2 update (the delayed Pfaffian accept makes no pass over A^{-1}:
+    its GEMV is in the propose, pf_propose_roofline).
     """
     bytes_per = (2 if delay < 2 else 1) * n * n * 8 * W
     if pf:
@@ -501,6 +502,30 @@ def run_pf_arm(L, torch, args, arm, F_d, pos0, slot_d, new_d, dist):
     return ratios_all, ms, clk, launches, prof, (delay, flush)
 
 
+def pf_propose_roofline(n, W, ms, hbm):
+    """The Pfaffian propose's pass over A^{-1} (A_0^{-1} in the delayed form):
+    X = A^{-1} x for the dense column of B = [x, e_i], n^2 FMA and n^2 x 8 B
+    per walker (the e_i column is a copy of one column; the delayed slot
+    corrections are n x 2K).  Bound: the FP64 pipe at n^2 FMA against HBM at
+    n^2 x 8 B, whichever takes longer."""
+    if not ms:
+        return None
+    byt, flop = n * n * 8.0 * W, 2.0 * n * n * W
+    t_hbm, t_fp64 = byt / (hbm * 1e9), flop / (FP64_PEAK_TFLOPS * 1e12)
+    out = {"bytes_per_launch": byt, "fp64_flop_per_launch": flop, "ms_per_launch": ms, "traffic": None,
+           "hbm": {"achieved": byt / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"},
+           "time_at_hbm_peak_ms": t_hbm * 1e3, "time_at_fp64_peak_ms": t_fp64 * 1e3}
+    out["hbm"]["frac"] = out["hbm"]["achieved"] / hbm
+    if t_fp64 > t_hbm:
+        ach = flop / (ms / 1e3) / 1e12
+        out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS})
+    else:
+        out.update({"bound": "hbm", "achieved": out["hbm"]["achieved"], "peak": hbm, "unit": "GB/s",
+                    "frac": out["hbm"]["frac"]})
+    return out
+
+
 def pf_flush_roofline(flush, n, W, K, ms_per_full, hbm):
     """One full skew flush of every walker: A_0^{-1} += P Q^T over K steps of
     2 slot columns (Eq. pf_delayed_Ainv), the upper half computed and
@@ -615,13 +640,16 @@ def main_pf(args, torch, L, rank, world, dist):
             L, torch, args, arm, F_d, pos0, slot_d, new_d, dist)
         arm_ratios[arm] = ratios_all
         acc_ms, acc_n = prof["accept"]
+        pro_ms, pro_n = prof["propose"]
         a = {"value": multigpu.whole_job_rate(W * args.steps, world, ms), "ms_per_step": ms / args.steps,
              "delay_K": delay, "flush": flush if delay >= 2 else None,
              "kernel_ms": {k: v[0] for k, v in prof.items()},
              "kernel_launches_timed": {k: v[1] for k, v in prof.items()},
              "gpu_launches": launches, "clocks": clk,
-             "accept_roofline": accept_roofline(delay, "native", n, W, acc_ms / acc_n if acc_n else None, hbm,
-                                                pf=True)}
+             "propose_roofline": pf_propose_roofline(n, W, pro_ms / pro_n if pro_n else None, hbm)}
+        if delay < 2:
+            a["accept_roofline"] = accept_roofline(delay, "native", n, W, acc_ms / acc_n if acc_n else None, hbm,
+                                                   pf=True)
         if delay >= 2:
             nfl = args.steps // delay
             a["flush_roofline"] = pf_flush_roofline(flush, n, W, delay, prof["flush"][0] / nfl if nfl else None, hbm)
@@ -639,7 +667,9 @@ def main_pf(args, torch, L, rank, world, dist):
     head = arms[main_arm]
     km = head["kernel_ms"]
     # the line's roofline belongs to the kernel class that takes the most time
-    cand = {"accept": (km.get("accept", 0.0), head["accept_roofline"])}
+    cand = {"propose": (km.get("propose", 0.0), head["propose_roofline"])}
+    if head.get("accept_roofline"):
+        cand["accept"] = (km.get("accept", 0.0), head["accept_roofline"])
     if head.get("flush_roofline"):
         cand["flush"] = (km.get("flush", 0.0), head["flush_roofline"])
     dom = max(cand, key=lambda k: cand[k][0])
