@@ -171,7 +171,7 @@ def cpu_baseline(Phi, occ0, slot, new, n, budget_s=15.0):
 # GPU arm
 # --------------------------------------------------------------------------
 FLUSH = {"native": 0, "tf32x3": 1, "tf32": 2, "bf16": 3, "bf16x3": 4, "df": 5, "split": 6}
-ARITH = {"native": 0, "df": 1}
+ARITH = {"native": 0, "df": 1, "mixed": 2}
 
 # name -> (delay, arith, flush); "delayed" is the headline form
 ARMS = {
@@ -180,6 +180,8 @@ ARMS = {
     "delayed_dfflush": (None, "native", "df"),     # FP64 GEMV, double-float flush (FP32 pipe)
     "delayed_tf32x3": (None, "native", "tf32x3"),  # FP64 GEMV, tensor-core TF32x3 flush (precision form)
     "delayed_dfgemv": (None, "df", "df"),          # double-float GEMV and flush
+    "delayed_mixed": (None, "mixed", "split"),     # half FP64 / half double-float GEMV, split-product flush
+    "delayed_dfgemv_split": (None, "df", "split"),  # double-float GEMV (thread per column), split-product flush
 }
 
 
@@ -318,17 +320,19 @@ def accept_roofline(delay, arith, n, W, ms, hbm, pf=False):
         flop_per = (6 if delay < 2 else 2) * n * n * W
     else:
         flop_per = (4 if delay < 2 else 2) * n * n * W
+    # FP64-pipe share of the products: all (native), half (mixed), none (double-float)
+    fp64_flop = flop_per * {"native": 1.0, "mixed": 0.5}.get(arith, 0.0)
     t_hbm = bytes_per / (hbm * 1e9)
-    t_fp64 = flop_per / (FP64_PEAK_TFLOPS * 1e12)
+    t_fp64 = fp64_flop / (FP64_PEAK_TFLOPS * 1e12)
     traffic = ACCEPT_DELAYED_TRAFFIC_PER_WALKER_N1024 * W if (
         not pf and delay >= 2 and arith == "native" and n == 1024) else None
-    out = {"bytes_per_launch": bytes_per, "fp64_flop_per_launch": flop_per if arith == "native" else 0,
+    out = {"bytes_per_launch": bytes_per, "fp64_flop_per_launch": fp64_flop,
            "ms_per_launch": ms, "traffic": traffic,
            "hbm": {"achieved": bytes_per / (ms / 1e3) / 1e9 if ms else None, "peak": hbm, "unit": "GB/s"},
            "time_at_hbm_peak_ms": t_hbm * 1e3, "time_at_fp64_peak_ms": t_fp64 * 1e3}
     out["hbm"]["frac"] = out["hbm"]["achieved"] / hbm if ms else None
-    if arith == "native" and t_fp64 > t_hbm:
-        ach = flop_per / (ms / 1e3) / 1e12 if ms else None
+    if fp64_flop and t_fp64 > t_hbm:
+        ach = fp64_flop / (ms / 1e3) / 1e12 if ms else None
         out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": ach / FP64_PEAK_TFLOPS if ms else None})
     else:

@@ -83,7 +83,8 @@ template <typename T>
 void launch_propose(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& U,
                     const DevOperand& V, const T* C, T* ratio_out, int* st_out, cudaStream_t st);
 template <typename T>
-void launch_accept(bool pf, bool delayed, bool df, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
+// arith: 0 dtype arithmetic, 1 double-float GEMV, 2 mixed FP64 / double-float GEMV (F64 only)
+void launch_accept(bool pf, bool delayed, int arith, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
                    const uint8_t* mask, const int* items, int nitems, cudaStream_t st);
 template <typename T>
 void launch_flush_native(bool pf, const DevLayout& L, const DevState<T>& S, const uint8_t* force_mask,

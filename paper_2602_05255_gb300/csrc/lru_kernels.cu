@@ -655,6 +655,112 @@ __global__ void __launch_bounds__(PT, 2) k_accept_delayed_lane(DevLayout L, DevS
     }
 }
 
+// Delayed accept of a real rank-1 update (b_tau equation of Sec. 2.3) with
+// the GEMV products taken off the FP64 pipe: one WARP per column l of
+// A_0^{-1}, so every load instruction reads 512 contiguous bytes (a thread
+// per column touches 32 cache lines per load, and the L1 lookups then bind
+// near 1.7 ms per pass at 1024 walkers, n = 1024).  Lane t holds the element
+// pairs p = t + 32 m of the column (NP2 16-byte loads in flight); each
+// element is split into hi + lo floats with integer operations and
+// multiplied into a double-float accumulator against the split of V
+// (shared memory).  MIXED: the even elements take one FP64 FMA each instead,
+// so the FP64 and the FP32 pipes share the pass; that partial sum joins the
+// double-float one before the warp reduction.  Lane 0 subtracts the slot
+// correction (V P) Q[l,:]^T in FP64 and writes z = y / r.  One CTA (8 warps)
+// per walker and CPB columns.
+struct alignas(16) VMix {
+    double ve;     // v_{2p}, FP64 (MIXED)
+    float oh, ol;  // hi + lo of v_{2p+1}
+};
+constexpr int DF_CPB = 64;   // columns per CTA of the warp-per-column double-float accept
+
+template <bool MIXED, int NP2>
+__global__ void __launch_bounds__(PT, 2) k_accept_delayed_warp_df(DevLayout L, DevState<double> S, DevOperand V,
+                                                                   const uint8_t* mask) {
+    __shared__ __align__(16) float4 sV4[32 * NP2];   // (hi v_2p, hi v_2p+1, lo v_2p, lo v_2p+1), or VMix
+    __shared__ double sVP[64];
+    const int w = blockIdx.x;
+    if (mask && !mask[w]) return;
+    if (S.pst[w] != 0) return;
+    const int n = L.nw(w);
+    const long long vo = L.vo(w);
+    const int Kc = L.Kc, cu = S.tau[w];
+    const int np = n >> 1;   // n is even
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const double* vb = vec_ptr<double>(V, L, w, 0, n);
+    for (int p = threadIdx.x; p < 32 * NP2; p += PT) {
+        const double v0 = p < np ? vb[2 * p] : 0.0, v1 = p < np ? vb[2 * p + 1] : 0.0;
+        float h0, l0, h1, l1;
+        split_d(v1, h1, l1);
+        if (MIXED) {
+            VMix m;
+            m.ve = v0;
+            m.oh = h1;
+            m.ol = l1;
+            reinterpret_cast<VMix*>(sV4)[p] = m;
+        } else {
+            split_d(v0, h0, l0);
+            sV4[p] = make_float4(h0, h1, l0, l1);
+        }
+    }
+    for (int c = threadIdx.x; c < cu; c += PT) sVP[c] = S.VP[(long long)w * MAXKK * Kc + c];
+    const double rinv = S.Rinv[(long long)w * MAXKK * MAXKK];
+    __syncthreads();
+    const double* Gw = S.G + L.mo(w);
+    const int l_end = min(n, (int)(blockIdx.y + 1) * DF_CPB);
+    for (int l = blockIdx.y * DF_CPB + wid; l < l_end; l += PT / 32) {
+        const double2* __restrict__ c2 = reinterpret_cast<const double2*>(Gw + (long long)l * n);
+        float ah0 = 0.f, al0 = 0.f, ah1 = 0.f, al1 = 0.f;
+        double a64 = 0.0, corr = 0.0;
+        // at most 16 loads in flight per lane (n = 2048: two batches per column)
+        constexpr int NB = NP2 < 16 ? NP2 : 16;
+#pragma unroll 1
+        for (int m0 = 0; m0 < NP2; m0 += NB) {
+            double2 g[NB];
+#pragma unroll
+            for (int m = 0; m < NB; ++m) {
+                const int p = lane + 32 * (m0 + m);
+                g[m] = p < np ? c2[p] : make_double2(0.0, 0.0);
+            }
+            if (m0 == 0 && lane == 0) {
+                // the slot correction, in FP64, while the loads are in flight
+                const double* qrow = S.Q + (vo + l) * Kc;
+                for (int c = 0; c < cu; ++c) corr = fma(sVP[c], qrow[c], corr);
+            }
+#pragma unroll
+            for (int m = 0; m < NB; ++m) {
+                const int p = lane + 32 * (m0 + m);
+                float gh, gl;
+                if (MIXED) {
+                    const VMix v = reinterpret_cast<const VMix*>(sV4)[p];
+                    a64 = fma(v.ve, g[m].x, a64);
+                    split_d(g[m].y, gh, gl);
+                    if (m & 1) df_fma(ah1, al1, v.oh, v.ol, gh, gl);
+                    else df_fma(ah0, al0, v.oh, v.ol, gh, gl);
+                } else {
+                    const float4 v = sV4[p];
+                    split_d(g[m].x, gh, gl);
+                    df_fma(ah0, al0, v.x, v.z, gh, gl);
+                    split_d(g[m].y, gh, gl);
+                    df_fma(ah1, al1, v.y, v.w, gh, gl);
+                }
+            }
+        }
+        if (MIXED) {
+            float h, lo;
+            split_d(a64, h, lo);
+            df_add(ah1, al1, h, lo);
+        }
+        df_add(ah0, al0, ah1, al1);
+        df_warp_sum(ah0, al0);
+        if (lane == 0) {
+            const double z = rinv * (df_to_double(ah0, al0) - corr);
+            S.Q[(vo + l) * Kc + cu] = z;
+            if (S.P32h) store_split(S, 1, (vo + l) * L.Kc32 + cu, z);
+        }
+    }
+}
+
 // Delayed accept of a real rank-1 update with the GEMV in double-float
 // arithmetic (FP32 pipe): per chunk l, y = V . chunk_l accumulated as hi+lo
 // floats from integer-split doubles, then in FP64 y -= (V P) Q[l,:]^T and
@@ -1268,8 +1374,9 @@ static void accept_npl(int npl, const DevLayout& L, const DevState<T>& S, const 
 }
 
 template <typename T>
-void launch_accept(bool pf, bool delayed, bool df, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
+void launch_accept(bool pf, bool delayed, int arith, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
                    const uint8_t* mask, const int* items, int nitems, cudaStream_t st) {
+    const bool df = arith != 0;
     const int nmax = L.n_max;
     int npl = 1;
     while (32 * npl < nmax) npl *= 2;
@@ -1278,7 +1385,23 @@ void launch_accept(bool pf, bool delayed, bool df, const DevLayout& L, const Dev
     if (nitems > 0) {
         bool done = false;
         if constexpr (std::is_same<T, double>::value) {
-            if (df && delayed && !pf && L.kk == 1 && !(V.mask & 1u) && L.n_max <= 2048) {
+            if (df && delayed && !pf && L.kk == 1 && L.kvec == nullptr && L.n_uni > 0 && !(V.mask & 1u) &&
+                L.n_uni <= 2048 && (L.n_uni % 2) == 0) {
+                // rank-1, uniform even n: one warp per column of A_0^{-1}
+                dim3 grid(L.W, (L.n_uni + DF_CPB - 1) / DF_CPB);
+                const int np2 = (L.n_uni / 2 + 31) / 32;
+#define LRU_ACC_WDF(N)                                                                        \
+    case N:                                                                                   \
+        if (arith == 2) k_accept_delayed_warp_df<true, N><<<grid, PT, 0, st>>>(L, S, V, mask); \
+        else k_accept_delayed_warp_df<false, N><<<grid, PT, 0, st>>>(L, S, V, mask);          \
+        break;
+                switch (np2 <= 4 ? 4 : (np2 <= 8 ? 8 : (np2 <= 16 ? 16 : 32))) {
+                    LRU_ACC_WDF(4) LRU_ACC_WDF(8) LRU_ACC_WDF(16) LRU_ACC_WDF(32) default: break;
+                }
+#undef LRU_ACC_WDF
+                done = true;
+            }
+            if (!done && df && delayed && !pf && L.kk == 1 && !(V.mask & 1u) && L.n_max <= 2048) {
                 const int4* it = reinterpret_cast<const int4*>(items);
 #define LRU_ACC_DF(N) \
     case N: k_accept_delayed_df<N><<<nitems, PT, 0, st>>>(L, S, V, mask, it); break;
@@ -1369,7 +1492,7 @@ void launch_commit_moves(int W, int n, int k, int* occ, const int* slot, const i
 #define LRU_INST(T)                                                                                          \
     template void launch_propose<T>(bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&,    \
                                     const DevOperand&, const T*, T*, int*, cudaStream_t);                   \
-    template void launch_accept<T>(bool, bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&, \
+    template void launch_accept<T>(bool, bool, int, const DevLayout&, const DevState<T>&, const DevOperand&, \
                                    const uint8_t*, const int*, int, cudaStream_t);                          \
     template void launch_flush_native<T>(bool, const DevLayout&, const DevState<T>&, const uint8_t*, int,   \
                                          cudaStream_t);                                                     \

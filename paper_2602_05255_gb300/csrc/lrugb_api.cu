@@ -40,7 +40,7 @@ struct lru_ctx {
     bool pf = false, delayed = false;
     int W = 0, kk = 0, K = 0, Kc = 0, Kc32 = 0, flush = 0;
     bool split_bf16 = false;
-    bool df = false;
+    int arith = 0;               // 0 dtype arithmetic, 1 double-float, 2 mixed (F64 only)
     int device = 0;
     cudaStream_t stream = nullptr;
     int n_uni = 0, n_max = 0;
@@ -214,7 +214,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     if (kk > MAXKK) return LRU_ERR_ARG;
     if (cfg->delay < 0) return LRU_ERR_ARG;
     if (cfg->flush < LRU_FLUSH_NATIVE || cfg->flush > LRU_FLUSH_SPLIT) return LRU_ERR_ARG;
-    if (cfg->arith != LRU_ARITH_NATIVE && cfg->arith != LRU_ARITH_DF) return LRU_ERR_ARG;
+    if (cfg->arith < LRU_ARITH_NATIVE || cfg->arith > LRU_ARITH_MIXED) return LRU_ERR_ARG;
     if (cfg->tile_chunks < 0) return LRU_ERR_ARG;
     if (cfg->refresh < LRU_REFRESH_AUTO || cfg->refresh > LRU_REFRESH_TENSOR) return LRU_ERR_ARG;
     const bool delayed = cfg->delay >= 2;
@@ -239,7 +239,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     h->Kc32 = bf16 ? (h->Kc + 63) / 64 * 64 : (h->Kc + 31) / 32 * 32;
     h->flush = cfg->flush;
     h->device = cfg->device;
-    h->df = cfg->arith == LRU_ARITH_DF && cfg->dtype == LRU_F64;
+    h->arith = cfg->dtype == LRU_F64 ? cfg->arith : LRU_ARITH_NATIVE;
 
     // geometry
     h->n_h.resize(h->W);
@@ -663,7 +663,7 @@ lru_status lru_accept(lru_handle h, const uint8_t* mask) {
     h->launches += (nitems > 0 ? 1 : 0) + 1;
     prof_begin(h, LRU_PROF_ACCEPT);
     LRU_DISPATCH(h, {
-        launch_accept<T>(h->pf, h->delayed, h->df, L, h->state<T>(), h->lastV, mask, h->d_items, nitems, h->stream);
+        launch_accept<T>(h->pf, h->delayed, h->arith, L, h->state<T>(), h->lastV, mask, h->d_items, nitems, h->stream);
     });
     prof_end(h, LRU_PROF_ACCEPT);
     lru_status s = cuda_check();
@@ -898,7 +898,8 @@ lru_status lru_launch_count(lru_handle h, int64_t* count) {
 
 static lru_status batched_dense(bool pf, int32_t dtype, int64_t W, int32_t n, const void* A, double* logabs,
                                 void* sign, void* stream) {
-    if (W < 1 || n < 1 || n > MAXN || !A || !logabs || !sign || dtype_size(dtype) == 0) return LRU_ERR_ARG;
+    if (W < 1 || W > (int64_t)INT32_MAX || n < 1 || n > MAXN || !A || !logabs || !sign || dtype_size(dtype) == 0)
+        return LRU_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0, nsm = 148;
     CK(cudaGetDevice(&dev));

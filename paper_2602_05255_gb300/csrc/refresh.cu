@@ -823,6 +823,7 @@ LRU_INST_R(c64)
 // ---------------------------------------------------------------------------
 
 #include <mutex>
+#include <stdint.h>
 
 #include "../../include/lrugb.h"
 
@@ -868,7 +869,7 @@ extern "C" lru_status lru_slogdet_batched_noalloc(int32_t dtype, int64_t W, int3
         case LRU_C64: sz = 8; break;
         default: return LRU_ERR_ARG;
     }
-    if (W < 1 || W > (int64_t)1 << 31 || n < 1 || n > 2048 || !A || !logabs || !sign) return LRU_ERR_ARG;
+    if (W < 1 || W > (int64_t)INT32_MAX || n < 1 || n > 2048 || !A || !logabs || !sign) return LRU_ERR_ARG;
     const size_t per = (size_t)n * n * sz;
     if (per > NOALLOC_SCRATCH_BYTES) return LRU_ERR_ARG;   // one matrix must fit the workspace
     int dev = 0, nsm = 148;

@@ -9,6 +9,11 @@ from oracle import lru_oracle as O  # noqa: E402
 from paper_2602_05255_gb300 import workloads  # noqa: E402
 
 RTOL_F64 = 1e-10
+# Ceiling of the conditioning-limited bar on chains over the paper's Slater
+# and pairing matrices (N(0, 1/n) entries): their condition numbers reach
+# ~1e6, where the oracle's own FP64 chain is up to 6e-9 away from the exact
+# ratio (checked against 200-bit arithmetic), a bar of 6e-8.
+CEIL_CHAIN = 1e-7
 
 
 def lrugb():
@@ -24,26 +29,75 @@ def rel(a, b):
     return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
 
 
-def check_ratios(gpu, chain, exact, base=RTOL_F64, what="", eps_scale=1.0):
-    """Ratio parity with a condition-aware bound.
+# One summary per check_ratios call, printed by the tests (pytest -s shows them):
+# (what, steps, near-node steps, conditioning-limited steps, largest bar used,
+#  largest GPU error against the oracle chain and against the exact ratio).
+PARITY_LOG = []
 
-    A step compares GPU and oracle-chain ratios with relative tolerance
-    max(base, 10 * eps_scale * e) where e is the largest |r_chain - r_exact| /
-    |r_exact| so far: the oracle chain's own accumulated FP64 rounding error
-    against the from-scratch ratios (large after near-node steps); eps_scale is the unit roundoff of the GPU
-    arithmetic over FP64's (256 for the double-float paths).  Near-node
-    steps (|r_exact| < 1e-6 median |r|) compare absolute errors against
-    base * median |r|."""
+
+def exact_det_ratio(A, U, V):
+    """det(A + U V) / det(A) = det(I + V A^{-1} U), with A^{-1} U from a fresh
+    LAPACK solve of the current matrix (more accurate than a quotient of two
+    slogdet values at ill-conditioned steps)."""
+    A, U, V = (np.asarray(x) for x in (A, U, V))
+    R = np.eye(U.shape[1], dtype=np.result_type(A, U, V)) + V @ np.linalg.solve(A, U)
+    return np.linalg.det(R) if R.shape[0] > 1 else R[0, 0]
+
+
+def exact_pf_ratio(A, B, C):
+    """pf(A + B C B^T) / pf(A) = pf(C^{-1} + B^T A^{-1} B) / pf(C^{-1}) (App. A.2),
+    with A^{-1} B from a fresh LAPACK solve of the current matrix and the
+    2k x 2k Pfaffians from the oracle's pairing sum."""
+    A, B, C = (np.asarray(x) for x in (A, B, C))
+    Ci = np.linalg.inv(C)
+    Ci = (Ci - Ci.T) / 2
+    M = Ci + B.T @ np.linalg.solve(A, B)
+    M = (M - M.T) / 2
+    return O.pf_pairings(M) / O.pf_pairings(Ci)
+
+
+def check_ratios(gpu, chain, exact, base=RTOL_F64, what="", eps_scale=1.0, refresh_every=0, ceiling=None):
+    """Ratio parity against the oracle's chain and against the exact ratios.
+
+    The bar is the relative error `base` (1e-10 in FP64), against both.  A
+    chain of low-rank updates carries the rounding of every update since the
+    last from-scratch refresh, amplified by the conditioning of the matrices
+    it passed through, and the oracle's own FP64 chain measures that amount:
+    e_run is its largest relative error against the exact ratio since the
+    last refresh (reset at every refresh).  A step where 10 * eps_scale * e_run
+    exceeds `base` is conditioning-limited, and its bar is 10 * eps_scale *
+    e_run; eps_scale is the unit roundoff of the GPU arithmetic over FP64's
+    (1 for FP64, 256 for the double-float paths).  The largest bar used must
+    stay within `ceiling` (default 100 * eps_scale * base).  Near-node steps
+    (|exact| < 1e-6 median |exact|) compare absolute errors against
+    base * median |exact|.  Returns the summary it appends to PARITY_LOG."""
     gpu, chain, exact = (np.asarray(x) for x in (gpu, chain, exact))
+    ceiling = 100.0 * eps_scale * base if ceiling is None else ceiling
     med = np.median(np.abs(exact))
-    e_run = 0.0   # rounding errors accumulate along a chain: the running maximum sets the scale
+    e_run = 0.0
+    out = {"what": str(what), "steps": len(exact), "near_node": 0, "cond_limited": 0, "max_bar": base,
+           "max_err_vs_chain": 0.0, "max_err_vs_exact": 0.0, "ceiling": ceiling}
     for s in range(len(exact)):
+        if refresh_every and s % refresh_every == 0:
+            e_run = 0.0
         if abs(exact[s]) < 1e-6 * med:
+            out["near_node"] += 1
             assert abs(gpu[s] - chain[s]) <= base * med, (what, s, gpu[s], chain[s], exact[s])
             continue
         e_run = max(e_run, abs(chain[s] - exact[s]) / abs(exact[s]))
-        tol = max(base, 10 * eps_scale * e_run)
-        assert abs(gpu[s] - chain[s]) <= tol * abs(chain[s]), (what, s, gpu[s], chain[s], exact[s], tol)
+        bar = max(base, 10 * eps_scale * e_run)
+        if bar > base:
+            out["cond_limited"] += 1
+        out["max_bar"] = max(out["max_bar"], bar)
+        ec = abs(gpu[s] - chain[s]) / abs(chain[s])
+        ee = abs(gpu[s] - exact[s]) / abs(exact[s])
+        out["max_err_vs_chain"] = max(out["max_err_vs_chain"], ec)
+        out["max_err_vs_exact"] = max(out["max_err_vs_exact"], ee)
+        assert ec <= bar and ee <= bar, (what, s, gpu[s], chain[s], exact[s], bar)
+    assert out["max_bar"] <= ceiling, (what, out)
+    PARITY_LOG.append(out)
+    print("parity:", out)
+    return out
 
 
 def fro_rel(a, b):

@@ -109,3 +109,14 @@ def test_null_arguments(lib):
     assert lib.lru_create(None, None) == 1
     assert lib.lru_destroy(None) == 1
     assert lib.lru_accept(None, None) == 1
+
+
+@pytest.mark.parametrize("name", ["lru_slogdet_batched", "lru_slogpf_batched", "lru_slogdet_batched_noalloc"])
+def test_batched_entry_points_reject_walker_counts_beyond_int32(lib, name):
+    # the kernels index walkers with 32-bit ints: 2^31 walkers is an argument
+    # error, found before any CUDA call (no pointer is dereferenced)
+    f = getattr(lib, name)
+    f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32] + [ctypes.c_void_p] * 4
+    f.restype = ctypes.c_int
+    for W in (2 ** 31, 2 ** 40, 0, -1):
+        assert f(0, W, 4, 16, 16, 16, None) == 1, W

@@ -68,12 +68,14 @@ def test_row_col_chain_matches_oracle(cplx, delay):
             assert np.array_equal(inv_gpu[w], -inv_gpu[w].T) or steps % delay != 0
 
 
+@pytest.mark.parametrize("k", [2, 4, 8])
 @pytest.mark.parametrize("delay", [0, 3])
-def test_general_C_rank2(delay):
-    # k = 2: dense B (n x 4) and a random invertible skew C per walker (App. A.2, Eq. pf_low_rank)
+def test_general_C_rank_k(k, delay):
+    # dense B (n x 2k) and a random invertible skew C per walker (App. A.2, Eq.
+    # pf_low_rank): the 2k x 2k Parlett-Reid core at 2k = 4, 8 and 16
     L = lrugb()
-    W, n, k, steps = 3, 24, 2, 7
-    g = np.random.Generator(np.random.PCG64(91))
+    W, n, steps = 3, 40, 7
+    g = np.random.Generator(np.random.PCG64(91 + k))
     A = g.standard_normal((W, n, n))
     A = A - A.transpose(0, 2, 1)
     st = L.LowRankState("pf", W, n, k=k, dtype=torch.float64, delay=delay)
@@ -81,7 +83,7 @@ def test_general_C_rank2(delay):
     cars = [O.init_pf_carrier(A[w], delay) if delay else None for w in range(W)]
     Ainv = [O.skew_part(O.inv(A[w])) for w in range(W)]
     for s in range(steps):
-        Bd = g.standard_normal((W, 2 * k, n)) * 0.3
+        Bd = g.standard_normal((W, 2 * k, n)) * (0.3 / np.sqrt(k))
         Cm = g.standard_normal((W, 2 * k, 2 * k))
         Cm = Cm - Cm.transpose(0, 2, 1)
         r, status = st.propose_pf(L.Operand(dense=tdev(Bd)), tdev(Cm))

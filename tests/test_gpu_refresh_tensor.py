@@ -9,7 +9,7 @@ the FP64 Gauss-Jordan and the tensor form differ by O(cond * 2^-53)).
 import numpy as np
 import pytest
 
-from gpu_common import O, check_ratios, det_workload, fro_rel, lrugb, tdev, torch
+from gpu_common import CEIL_CHAIN, O, check_ratios, det_workload, fro_rel, lrugb, tdev, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -118,7 +118,7 @@ def test_delayed_chain_with_tensor_refresh_matches_oracle():
             occ[slot[s, w]] = new[s, w]
             if (s + 1) % every == 0:
                 car = O.init_det_carrier(O.slater_matrix(Phi, occ), K)
-        check_ratios(ratios[:, w], chain, exact, what=w)
+        check_ratios(ratios[:, w], chain, exact, what=w, refresh_every=every, ceiling=CEIL_CHAIN)
         assert fro_rel(inv[w], O.carrier_inverse(car)) <= 1e-10
     st.check_device_error()
 

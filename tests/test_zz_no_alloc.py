@@ -42,20 +42,51 @@ def _call(torch, f, dtype_code, A):
     return code, logabs.cpu().numpy(), sign.cpu().numpy()
 
 
-@pytest.mark.parametrize("cplx", [False, True])
-def test_noalloc_matches_allocating_entry_point_twice(cplx):
+# dtype code, numpy dtype, relative tolerance on log|det| against the oracle
+DTYPES = {"f64": (0, np.float64, 1e-12), "c128": (1, np.complex128, 1e-12),
+          "f32": (2, np.float32, 1e-4), "c64": (3, np.complex64, 1e-4)}
+
+
+@pytest.mark.parametrize("dt", list(DTYPES))
+def test_noalloc_matches_allocating_entry_point_twice(dt):
+    from oracle import lru_oracle as O
     torch, lib = _lib()
+    code_dt, npdt, rtol = DTYPES[dt]
+    cplx = np.iscomplexobj(np.zeros(1, npdt))
     g = np.random.Generator(np.random.PCG64(2024))
-    dtype_code = 1 if cplx else 0
-    # two calls in a row with different sizes: the second must not see the first's contents
+    # two calls in a row with different sizes: the second must not see the
+    # first's contents; A = 3 I + N(0, 1/n) keeps the single-precision cases
+    # well conditioned
     for W, n in ((300, 96), (7, 513)):
         A = g.standard_normal((W, n, n)) + (1j * g.standard_normal((W, n, n)) if cplx else 0)
+        A = (A / np.sqrt(n) + 3 * np.eye(n)).astype(npdt)
         At = torch.tensor(A, device="cuda")
-        c0, l0, s0 = _call(torch, lib.lru_slogdet_batched, dtype_code, At)
-        c1, l1, s1 = _call(torch, lib.lru_slogdet_batched_noalloc, dtype_code, At)
+        c0, l0, s0 = _call(torch, lib.lru_slogdet_batched, code_dt, At)
+        c1, l1, s1 = _call(torch, lib.lru_slogdet_batched_noalloc, code_dt, At)
         assert c0 == 0 and c1 == 0
-        assert np.allclose(l1, l0, rtol=1e-12, atol=0)
-        assert np.allclose(s1, s0, rtol=0, atol=1e-12)
+        assert np.allclose(l1, l0, rtol=rtol, atol=0)
+        assert np.allclose(s1, s0, rtol=0, atol=rtol)
+        for w in (0, W - 1):
+            s_ref, l_ref = O.slogdet(A[w].astype(np.complex128 if cplx else np.float64))
+            assert abs(l1[w] - l_ref) <= rtol * max(1.0, abs(l_ref)), (dt, n, w)
+            assert abs(s1[w] - s_ref) <= 10 * rtol, (dt, n, w)
+
+
+def test_noalloc_one_slot_at_the_workspace_limit():
+    # n = 2048 in complex128 is 64 MiB per matrix: the whole workspace holds one
+    # slot, which the two walkers share in turn
+    from oracle import lru_oracle as O
+    torch, lib = _lib()
+    g = np.random.Generator(np.random.PCG64(2025))
+    W, n = 2, 2048
+    A = (g.standard_normal((W, n, n)) + 1j * g.standard_normal((W, n, n))) / np.sqrt(n) + 3 * np.eye(n)
+    At = torch.tensor(A, device="cuda")
+    c0, l0, s0 = _call(torch, lib.lru_slogdet_batched, 1, At)
+    c1, l1, s1 = _call(torch, lib.lru_slogdet_batched_noalloc, 1, At)
+    assert c0 == 0 and c1 == 0
+    assert np.allclose(l1, l0, rtol=1e-12, atol=0) and np.allclose(s1, s0, rtol=0, atol=1e-12)
+    s_ref, l_ref = O.slogdet(A[1])
+    assert abs(l1[1] - l_ref) <= 1e-11 * abs(l_ref) and abs(s1[1] - s_ref) <= 1e-10
 
 
 def test_noalloc_rejects_sizes_beyond_its_workspace():
