@@ -171,7 +171,7 @@ def cpu_baseline(Phi, occ0, slot, new, n, budget_s=15.0):
 # GPU arm
 # --------------------------------------------------------------------------
 FLUSH = {"native": 0, "tf32x3": 1, "tf32": 2, "bf16": 3, "bf16x3": 4, "df": 5, "split": 6}
-ARITH = {"native": 0, "df": 1, "mixed": 2}
+ARITH = {"native": 0, "df": 1}
 
 # name -> (delay, arith, flush); "delayed" is the headline form
 ARMS = {
@@ -180,7 +180,6 @@ ARMS = {
     "delayed_dfflush": (None, "native", "df"),     # FP64 GEMV, double-float flush (FP32 pipe)
     "delayed_tf32x3": (None, "native", "tf32x3"),  # FP64 GEMV, tensor-core TF32x3 flush (precision form)
     "delayed_dfgemv": (None, "df", "df"),          # double-float GEMV and flush
-    "delayed_mixed": (None, "mixed", "split"),     # half FP64 / half double-float GEMV, split-product flush
     "delayed_dfgemv_split": (None, "df", "split"),  # double-float GEMV (thread per column), split-product flush
 }
 
@@ -311,17 +310,20 @@ def accept_roofline(delay, arith, n, W, ms, hbm, pf=False):
     n^2 FMA.  The bound is whichever takes longer at its peak (HBM copy
     bandwidth, FP64 pipe); the double-float GEMV runs on the FP32 pipe and is
     reported against HBM.  Pfaffian row-and-column move (B = [x, e_i]), plain
-    form: n^2 FMA for x^T A^{-1} (the e_i column is a read) plus 2 n^2 for the
-    rank-2 update (the delayed Pfaffian accept makes no pass over A^{-1}:
-    its GEMV is in the propose, pf_propose_roofline).
+    form: the exactly skew update A^{-1} + X M^{-1} X^T reads the upper
+    triangle and writes both (1.5 n^2 x 8 B) with 2 FMA per upper element
+    (2 n^2 flop); the delayed Pfaffian accept makes no pass over A^{-1}: its
+    GEMV is in the propose, pf_propose_roofline.
     """
     bytes_per = (2 if delay < 2 else 1) * n * n * 8 * W
+    if pf and delay < 2:
+        bytes_per = 1.5 * n * n * 8 * W
     if pf:
-        flop_per = (6 if delay < 2 else 2) * n * n * W
+        flop_per = 2 * n * n * W
     else:
         flop_per = (4 if delay < 2 else 2) * n * n * W
-    # FP64-pipe share of the products: all (native), half (mixed), none (double-float)
-    fp64_flop = flop_per * {"native": 1.0, "mixed": 0.5}.get(arith, 0.0)
+    # FP64-pipe share of the products: all (native), none (double-float)
+    fp64_flop = flop_per if arith == "native" else 0.0
     t_hbm = bytes_per / (hbm * 1e9)
     t_fp64 = fp64_flop / (FP64_PEAK_TFLOPS * 1e12)
     traffic = ACCEPT_DELAYED_TRAFFIC_PER_WALKER_N1024 * W if (
@@ -444,9 +446,11 @@ def load_peaks():
 # name -> (delay, flush): plain FP64 Woodbury step (Eq. pf_inv), delayed form
 # (Sec. 3.3) with the skew FP64 flush or the double-float skew flush
 PF_ARMS = {
-    "plain": (0, "native"),
-    "delayed": (None, "native"),
-    "delayed_dfflush": (None, "df"),
+    "plain": (0, "native", "native"),                 # FP64 propose, exactly skew rank-2 accept (Eq. pf_inv)
+    "delayed": (None, "native", "native"),            # FP64 propose, FP64 skew flush (Eq. pf_delayed_Ainv)
+    "delayed_dfflush": (None, "native", "df"),        # FP64 propose, double-float skew flush
+    "plain_dfprop": (0, "df", "native"),              # double-float pass X = A^{-1} x, skew accept
+    "delayed_df": (None, "df", "df"),                 # double-float pass and flush
 }
 PF_METRIC = "walker-updates/sec, Pfaffian rank-2 row-and-column moves (delayed vs plain, same GPU); roofline fraction"
 
@@ -469,10 +473,10 @@ def pf_workload_name(args):
             + (f"refresh every {args.refresh_every}" if args.refresh_every else "no refresh"))
 
 
-def pf_state(L, torch, args, delay, flush, F_d, pos0):
+def pf_state(L, torch, args, delay, flush, F_d, pos0, arith="native"):
     """A Pfaffian handle initialised from F[pos][:, pos], with its move buffers."""
     W, n = args.walkers, args.n
-    st = L.LowRankState("pf", W, n, k=1, dtype=torch.float64, delay=delay, flush=FLUSH[flush])
+    st = L.LowRankState("pf", W, n, k=1, dtype=torch.float64, delay=delay, flush=FLUSH[flush], arith=ARITH[arith])
     pos_d = torch.tensor(pos0, device="cuda")
     A = st.gather_pairs(F_d, pos_d)
     st.init(A)
@@ -485,9 +489,9 @@ def pf_state(L, torch, args, delay, flush, F_d, pos0):
 def run_pf_arm(L, torch, args, arm, F_d, pos0, slot_d, new_d, dist):
     W = args.walkers
     dev = torch.cuda.current_device()
-    delay, flush = PF_ARMS[arm]
+    delay, arith, flush = PF_ARMS[arm]
     delay = args.delay if delay is None else delay
-    st, pos_d, A, B, idx, B_op = pf_state(L, torch, args, delay, flush, F_d, pos0)
+    st, pos_d, A, B, idx, B_op = pf_state(L, torch, args, delay, flush, F_d, pos0, arith)
     ratio = torch.empty(W, dtype=torch.float64, device="cuda")
     ratios_all = torch.empty(args.steps, W, dtype=torch.float64, device="cuda")
     status = torch.empty(W, dtype=torch.int32, device="cuda")
@@ -503,18 +507,19 @@ def run_pf_arm(L, torch, args, arm, F_d, pos0, slot_d, new_d, dist):
 
     ms, clk, launches, prof = timed_steps(torch, st, step, args, dist, dev)
     st.close()
-    return ratios_all, ms, clk, launches, prof, (delay, flush)
+    return ratios_all, ms, clk, launches, prof, (delay, arith, flush)
 
 
-def pf_propose_roofline(n, W, ms, hbm):
+def pf_propose_roofline(n, W, ms, hbm, arith="native"):
     """The Pfaffian propose's pass over A^{-1} (A_0^{-1} in the delayed form):
     X = A^{-1} x for the dense column of B = [x, e_i], n^2 FMA and n^2 x 8 B
     per walker (the e_i column is a copy of one column; the delayed slot
     corrections are n x 2K).  Bound: the FP64 pipe at n^2 FMA against HBM at
-    n^2 x 8 B, whichever takes longer."""
+    n^2 x 8 B, whichever takes longer; in double-float arithmetic the
+    products run on the FP32 pipe and HBM binds."""
     if not ms:
         return None
-    byt, flop = n * n * 8.0 * W, 2.0 * n * n * W
+    byt, flop = n * n * 8.0 * W, (2.0 * n * n * W if arith == "native" else 0.0)
     t_hbm, t_fp64 = byt / (hbm * 1e9), flop / (FP64_PEAK_TFLOPS * 1e12)
     out = {"bytes_per_launch": byt, "fp64_flop_per_launch": flop, "ms_per_launch": ms, "traffic": None,
            "hbm": {"achieved": byt / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"},
@@ -533,14 +538,14 @@ def pf_propose_roofline(n, W, ms, hbm):
 def pf_flush_roofline(flush, n, W, K, ms_per_full, hbm):
     """One full skew flush of every walker: A_0^{-1} += P Q^T over K steps of
     2 slot columns (Eq. pf_delayed_Ainv), the upper half computed and
-    mirrored, n (n + 1) / 2 x 2K FMA per walker, reading and writing
-    A_0^{-1} once (2 n^2 x 8 B).  The FP64 flush is bound by the FP64 pipe;
+    mirrored, n (n + 1) / 2 x 2K FMA per walker, reading the upper half of
+    A_0^{-1} and writing both (1.5 n^2 x 8 B).  The FP64 flush is bound by the FP64 pipe;
     the double-float flush runs on the FP32 pipe and is reported against HBM
     with its FP64-equivalent rate."""
     if not ms_per_full:
         return None
     flop = 2.0 * (n * (n + 1) / 2) * 2 * K * W
-    byt = 2.0 * n * n * 8 * W
+    byt = 1.5 * n * n * 8 * W
     out = {"flop_per_full_flush": flop, "bytes_per_full_flush": byt, "ms_per_full_flush": ms_per_full,
            "fp64_equivalent_tflops": flop / (ms_per_full / 1e3) / 1e12,
            "hbm": {"achieved": byt / (ms_per_full / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"}}
@@ -640,17 +645,17 @@ def main_pf(args, torch, L, rank, world, dist):
     arms, arm_ratios = {}, {}
     order = [a.strip() for a in args.arms.split(",") if a.strip()]
     for arm in order:
-        ratios_all, ms, clk, launches, prof, (delay, flush) = run_pf_arm(
+        ratios_all, ms, clk, launches, prof, (delay, arith, flush) = run_pf_arm(
             L, torch, args, arm, F_d, pos0, slot_d, new_d, dist)
         arm_ratios[arm] = ratios_all
         acc_ms, acc_n = prof["accept"]
         pro_ms, pro_n = prof["propose"]
         a = {"value": multigpu.whole_job_rate(W * args.steps, world, ms), "ms_per_step": ms / args.steps,
-             "delay_K": delay, "flush": flush if delay >= 2 else None,
+             "delay_K": delay, "propose_arith": arith, "flush": flush if delay >= 2 else None,
              "kernel_ms": {k: v[0] for k, v in prof.items()},
              "kernel_launches_timed": {k: v[1] for k, v in prof.items()},
              "gpu_launches": launches, "clocks": clk,
-             "propose_roofline": pf_propose_roofline(n, W, pro_ms / pro_n if pro_n else None, hbm)}
+             "propose_roofline": pf_propose_roofline(n, W, pro_ms / pro_n if pro_n else None, hbm, arith)}
         if delay < 2:
             a["accept_roofline"] = accept_roofline(delay, "native", n, W, acc_ms / acc_n if acc_n else None, hbm,
                                                    pf=True)

@@ -87,11 +87,9 @@ typedef enum {
 /* Arithmetic of the streaming passes over A^{-1} for F64 handles. */
 typedef enum {
     LRU_ARITH_NATIVE = 0,   /* FP64 FMAs */
-    LRU_ARITH_DF = 1,       /* double-float (pairs of FP32) from integer-split FP64 data; the
-                               delayed GEMV of rank-1 determinant updates uses it */
-    LRU_ARITH_MIXED = 2     /* delayed rank-1 determinant GEMV with half of its products as FP64 FMAs
-                               and half in double-float, so the FP64 and FP32 pipes share the pass
-                               (uniform even n); elsewhere as LRU_ARITH_DF */
+    LRU_ARITH_DF = 1        /* double-float (pairs of FP32) from integer-split FP64 data, about 2^7 x
+                               FP64's rounding: the delayed GEMV of rank-1 determinant updates
+                               (HBM-bound instead of FP64-bound) and the Pfaffian propose's pass */
 } lru_arith;
 
 /* How init and refresh compute the FP64 inverse (F64 determinant handles):

@@ -94,9 +94,13 @@ template <typename R> LRU_D cplx<R> s_recip(cplx<R> a) {
     R d = ar * ar + ai * ai;
     return {ar / (d * s), -ai / (d * s)};
 }
-LRU_D double s_neg(double a) { return -a; }
-LRU_D float s_neg(float a) { return -a; }
-template <typename R> LRU_D cplx<R> s_neg(cplx<R> a) { return {-a.re, -a.im}; }
+// negation as a flip of the sign bit with an integer instruction: a
+// materialised FP64 negation would take a slot of the (narrow) FP64 pipe
+LRU_D double s_neg(double a) {
+    return __hiloint2double(__double2hiint(a) ^ (int)0x80000000, __double2loint(a));
+}
+LRU_D float s_neg(float a) { return __int_as_float(__float_as_int(a) ^ (int)0x80000000); }
+template <typename R> LRU_D cplx<R> s_neg(cplx<R> a) { return {s_neg(a.re), s_neg(a.im)}; }
 LRU_D double s_half(double a) { return 0.5 * a; }
 LRU_D float s_half(float a) { return 0.5f * a; }
 template <typename R> LRU_D cplx<R> s_half(cplx<R> a) { return {R(0.5) * a.re, R(0.5) * a.im}; }

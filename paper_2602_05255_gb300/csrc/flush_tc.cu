@@ -113,7 +113,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     const uint32_t tx_bytes = 4u * nkc * CHUNK_BYTES;
 
     uint32_t phase = 0;
-    long long offset = 0;   // running index over the concatenated tile list
+    // this CTA's first tile of the current walker: (blockIdx.x - tiles of the
+    // earlier due walkers) mod gridDim.x, advanced in 32 bits per due walker
+    int first = (int)blockIdx.x;
     for (int w = 0; w < L.W && !s_abort; ++w) {
         const int t = tau[w];
         const bool go = force ? (force[w] && t > 0) : (t >= L.K);
@@ -124,9 +126,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         const long long vo = L.vo(w);
         double* Gw = G + L.mo(w);
         // tiles of this walker owned by this CTA
-        long long first = ((long long)blockIdx.x - offset) % gridDim.x;
-        if (first < 0) first += gridDim.x;
-        for (long long ti = first; ti < ntiles; ti += gridDim.x) {
+        for (int ti = first; ti < ntiles; ti += gridDim.x) {
             int tJ, tL;
             if (PF) {
                 // row-major enumeration of the upper triangle J <= L
@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
         }
-        offset += ntiles;
+        first -= ntiles % (int)gridDim.x;
+        if (first < 0) first += gridDim.x;
     }
     __syncthreads();
     if (warp == 0) {

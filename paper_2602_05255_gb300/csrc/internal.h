@@ -61,6 +61,7 @@ struct DevOperand {
     const int* idx;
     unsigned mask;   // bit a: slot a is one-hot
     int slots;       // vector slots per walker in the buffers (kmax)
+    int pre = -1;    // dense slot whose A^{-1} u_a a separate pass has already written to X (-1: none)
 };
 
 // Control block of the persistent fused step (see k_step).
@@ -79,12 +80,13 @@ struct StepCtl {
 };
 
 // ---- launchers (defined in lru_kernels.cu, instantiated for every dtype) ----
+// df: the pass over A^{-1} for a single dense column in double-float arithmetic (F64 only)
 template <typename T>
-void launch_propose(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& U,
+void launch_propose(bool pf, bool delayed, bool df, const DevLayout& L, const DevState<T>& S, const DevOperand& U,
                     const DevOperand& V, const T* C, T* ratio_out, int* st_out, cudaStream_t st);
 template <typename T>
-// arith: 0 dtype arithmetic, 1 double-float GEMV, 2 mixed FP64 / double-float GEMV (F64 only)
-void launch_accept(bool pf, bool delayed, int arith, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
+// df: the delayed rank-1 determinant GEMV in double-float arithmetic (F64 only)
+void launch_accept(bool pf, bool delayed, bool df, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
                    const uint8_t* mask, const int* items, int nitems, cudaStream_t st);
 template <typename T>
 void launch_flush_native(bool pf, const DevLayout& L, const DevState<T>& S, const uint8_t* force_mask,

@@ -85,23 +85,33 @@ __device__ void block_reduce_vec(T (&v)[NV], T* red, T* out) {
 // and takes the tiles whose global index is congruent to its block index.
 // Pfaffian tiles cover J <= L only.
 struct TileIter {
-    long long offset = 0;
+    int first_ = -1;             // (blockIdx.x - tiles of the earlier due walkers) mod gridDim.x
+    int last_nt = -1, last_d = 0;
     __device__ static int tiles(int nt, bool pf) { return pf ? nt * (nt + 1) / 2 : nt * nt; }
-    __device__ static void coords(long long ti, int nt, bool pf, int& tJ, int& tL) {
+    __device__ static void coords(int ti, int nt, bool pf, int& tJ, int& tL) {
         if (pf) {
-            int r = 0, rem = (int)ti;
+            int r = 0, rem = ti;
             while (rem >= nt - r) { rem -= nt - r; ++r; }
             tJ = r;
             tL = r + rem;
         } else {
-            tJ = (int)(ti % nt);
-            tL = (int)(ti / nt);
+            tL = ti / nt;
+            tJ = ti - tL * nt;
         }
     }
-    __device__ long long first(int ntiles) {
-        long long f = ((long long)blockIdx.x - offset) % gridDim.x;
-        if (f < 0) f += gridDim.x;
-        offset += ntiles;
+    // kept in 32 bits and advanced by one subtraction per due walker: a 64-bit
+    // modulo here, run by every thread of every CTA for every due walker,
+    // cost more instructions than the flush arithmetic itself
+    __device__ int first(int ntiles) {
+        const int G = (int)gridDim.x;
+        if (first_ < 0) first_ = (int)blockIdx.x;
+        const int f = first_;
+        if (ntiles != last_nt) {
+            last_nt = ntiles;
+            last_d = ntiles % G;
+        }
+        first_ -= last_d;
+        if (first_ < 0) first_ += G;
         return f;
     }
 };
@@ -239,7 +249,7 @@ __device__ void propose_walker(const int w, const DevLayout L, const DevState<T>
         // dense columns, four at a time
         int dl[MAXKK], nd = 0;
         for (int a = 0; a < kk; ++a)
-            if (s_iu[a] < 0) dl[nd++] = a;
+            if (s_iu[a] < 0 && a != U.pre) dl[nd++] = a;
         if (nd == 1) {
             // one dense column (the Pfaffian row-and-column move, a rank-1
             // dense update): each thread walks the columns for its rows with
@@ -429,6 +439,112 @@ __device__ void propose_walker(const int w, const DevLayout L, const DevState<T>
     }
 }
 
+// X_a = A^{-1} u_a for the one dense column a of a proposal (the Pfaffian
+// row-and-column move B = [x, e_i], a rank-1 dense update), before the
+// propose kernel, which then skips that column.  One CTA per walker; thread t
+// owns rows t + PT r (r < NR) and walks the columns of A^{-1} (contiguous in
+// the rows, so every load is coalesced) with two independent accumulators per
+// row (the column range split in halves) and few registers, so that many
+// CTAs per SM hide the load latency.  DF (real FP64 only): the products in
+// double-float arithmetic on the FP32 pipe (integer-split elements against
+// the split u), so the pass is bound by HBM instead of the FP64 pipe.
+template <typename T, int NR, bool DF>
+__global__ void __launch_bounds__(PT, 4) k_dense_column(DevLayout L, DevState<T> S, DevOperand U, int a) {
+    __shared__ T su[2048];
+    __shared__ float2 suf[DF ? 2048 : 1];
+    const int w = blockIdx.x;
+    const int n = L.nw(w);
+    const T* u = vec_ptr<T>(U, L, w, a, n);
+    for (int l = threadIdx.x; l < n; l += PT) {
+        su[l] = u[l];
+        if constexpr (DF) {
+            float h, lo;
+            split_d((double)u[l], h, lo);
+            suf[l] = make_float2(h, lo);
+        }
+    }
+    __syncthreads();
+    const T* G = S.G + L.mo(w);
+    T* Xa = S.X + L.vo(w) * L.kk + (long long)a * n;
+    const int h = n / 2;
+    if constexpr (DF) {
+        float ah0[NR], al0[NR], ah1[NR], al1[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) ah0[r] = al0[r] = ah1[r] = al1[r] = 0.f;
+#pragma unroll 4
+        for (int l = 0; l < h; ++l) {
+            const double* c0 = reinterpret_cast<const double*>(G) + (long long)l * n;
+            const double* c1 = reinterpret_cast<const double*>(G) + (long long)(l + h) * n;
+            const float2 u0 = suf[l], u1 = suf[l + h];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int j = threadIdx.x + PT * r;
+                if (j < n) {
+                    float gh, gl;
+                    split_d(c0[j], gh, gl);
+                    df_fma(ah0[r], al0[r], u0.x, u0.y, gh, gl);
+                    split_d(c1[j], gh, gl);
+                    df_fma(ah1[r], al1[r], u1.x, u1.y, gh, gl);
+                }
+            }
+        }
+        if (n & 1) {
+            const double* c = reinterpret_cast<const double*>(G) + (long long)(n - 1) * n;
+            const float2 ul = suf[n - 1];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int j = threadIdx.x + PT * r;
+                if (j < n) {
+                    float gh, gl;
+                    split_d(c[j], gh, gl);
+                    df_fma(ah0[r], al0[r], ul.x, ul.y, gh, gl);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int j = threadIdx.x + PT * r;
+            df_add(ah0[r], al0[r], ah1[r], al1[r]);
+            if (j < n) reinterpret_cast<double*>(Xa)[j] = df_to_double(ah0[r], al0[r]);
+        }
+        return;
+    } else {
+        T acc0[NR], acc1[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            acc0[r] = s_zero(T());
+            acc1[r] = s_zero(T());
+        }
+#pragma unroll 4
+        for (int l = 0; l < h; ++l) {
+            const T* c0 = G + (long long)l * n;
+            const T* c1 = G + (long long)(l + h) * n;
+            const T u0 = su[l], u1 = su[l + h];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int j = threadIdx.x + PT * r;
+                if (j < n) {
+                    acc0[r] = s_fma(c0[j], u0, acc0[r]);
+                    acc1[r] = s_fma(c1[j], u1, acc1[r]);
+                }
+            }
+        }
+        if (n & 1) {
+            const T* c = G + (long long)(n - 1) * n;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int j = threadIdx.x + PT * r;
+                if (j < n) acc0[r] = s_fma(c[j], su[n - 1], acc0[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int j = threadIdx.x + PT * r;
+            if (j < n) Xa[j] = acc0[r] + acc1[r];
+        }
+    }
+}
+
 template <typename T, bool PF, bool DELAYED>
 __global__ void __launch_bounds__(PT) k_propose(DevLayout L, DevState<T> S, DevOperand U, DevOperand V,
                                                  const T* C, T* ratio_out, int* st_out) {
@@ -589,6 +705,82 @@ __global__ void __launch_bounds__(PT, 2) k_accept(DevLayout L, DevState<T> S, De
     accept_item<T, DELAYED, NPL, KKS>(items[blockIdx.x], L, S, V, mask);
 }
 
+// Plain Pfaffian accept in skew form (Eq. pf_inv with (A^{-1})^T = -A^{-1}):
+//   A'^{-1} = A^{-1} + X M^{-1} X^T,   X = A^{-1} B (from the propose),
+// with M^{-1} projected onto its skew part.  Only the upper triangle j < l is
+// computed, one FMA per element and column of B against
+// Z_l = M^{-1} X_l^T (per column); the lower triangle is written as the exact
+// negative of the upper one and the diagonal as zero, so A^{-1} stays exactly
+// skew along the chain.  That halves the FP64 work of the generic Woodbury
+// pass (which also reduces B^T A^{-1} across lanes) and reads only the upper
+// half.  One CTA per (walker, 32 x 32 upper tile).
+template <typename T>
+__global__ void __launch_bounds__(256) k_accept_pf_skew(DevLayout L, DevState<T> S, const uint8_t* mask) {
+    __shared__ T sXj[32][MAXKK + 1];   // X rows of the tile's j range
+    __shared__ T sZl[32][MAXKK + 1];   // Z = M^{-1} X^T rows of the tile's l range
+    __shared__ T sMi[MAXKK * MAXKK];
+    __shared__ T sT[32][33];
+    const int w = blockIdx.y;
+    if (mask && !mask[w]) return;
+    if (S.pst[w] != 0) return;
+    const int n = L.nw(w), kk = L.kv(w);
+    const int nt = (n + 31) / 32;
+    if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
+    int tJ, tL;
+    TileIter::coords((int)blockIdx.x, nt, true, tJ, tL);
+    const int j0 = tJ * 32, l0 = tL * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    const T* X = S.X + L.vo(w) * L.kk;                        // kk vectors of n
+    const T* Ri = S.Rinv + (long long)w * MAXKK * MAXKK;
+    for (int e = threadIdx.x; e < kk * kk; e += 256) {
+        const int a = e / kk, b = e % kk;
+        sMi[a * MAXKK + b] = s_half(Ri[a * MAXKK + b] - Ri[b * MAXKK + a]);   // skew part
+    }
+    for (int e = threadIdx.x; e < 32 * kk; e += 256) {
+        const int a = e / 32, r = e % 32;
+        sXj[r][a] = (j0 + r < n) ? X[(long long)a * n + j0 + r] : s_zero(T());
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * kk; e += 256) {
+        const int a = e / 32, r = e % 32;
+        T z = s_zero(T());
+        if (l0 + r < n)
+            for (int b = 0; b < kk; ++b) z = s_fma(sMi[a * MAXKK + b], X[(long long)b * n + l0 + r], z);
+        sZl[r][a] = z;
+    }
+    __syncthreads();
+    T* Gw = S.G + L.mo(w);
+    const int j = j0 + tx;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int rl = ty + 8 * q, l = l0 + rl;
+        T v = s_zero(T());
+        if (j < n && l < n && (tJ != tL || tx < rl)) {
+            v = Gw[(long long)l * n + j];   // (A^{-1})_{jl}, j < l
+            for (int a = 0; a < kk; ++a) v = s_fma(sXj[tx][a], sZl[rl][a], v);
+        }
+        sT[rl][tx] = v;
+    }
+    __syncthreads();
+    // (j, l), j < l: the computed value; (l, j): its exact negative; diagonal 0
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int rl = ty + 8 * q, l = l0 + rl;
+        if (j >= n || l >= n) continue;
+        if (tJ != tL || tx < rl) Gw[(long long)l * n + j] = sT[rl][tx];
+        else if (tx == rl) Gw[(long long)l * n + j] = s_zero(T());
+        else Gw[(long long)l * n + j] = s_neg(sT[tx][rl]);   // diagonal tile, j > l
+    }
+    if (tJ != tL) {
+        // mirror tile: (l, j) for l in the L range, stored at G[j * n + l]
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int rj = ty + 8 * q, jj = j0 + rj, ll = l0 + tx;
+            if (jj < n && ll < n) Gw[(long long)jj * n + ll] = s_neg(sT[tx][rj]);
+        }
+    }
+}
+
 // Delayed accept of a rank-1 update, GEMV in the handle dtype with one THREAD
 // per column l of A_0^{-1}: the thread streams its contiguous column in
 // 16-byte loads against V (shared memory, broadcast), so the dot product
@@ -660,25 +852,28 @@ __global__ void __launch_bounds__(PT, 2) k_accept_delayed_lane(DevLayout L, DevS
 // A_0^{-1}, so every load instruction reads 512 contiguous bytes (a thread
 // per column touches 32 cache lines per load, and the L1 lookups then bind
 // near 1.7 ms per pass at 1024 walkers, n = 1024).  Lane t holds the element
-// pairs p = t + 32 m of the column (NP2 16-byte loads in flight); each
-// element is split into hi + lo floats with integer operations and
-// multiplied into a double-float accumulator against the split of V
-// (shared memory).  MIXED: the even elements take one FP64 FMA each instead,
-// so the FP64 and the FP32 pipes share the pass; that partial sum joins the
-// double-float one before the warp reduction.  Lane 0 subtracts the slot
-// correction (V P) Q[l,:]^T in FP64 and writes z = y / r.  One CTA (8 warps)
-// per walker and CPB columns.
-struct alignas(16) VMix {
-    double ve;     // v_{2p}, FP64 (MIXED)
-    float oh, ol;  // hi + lo of v_{2p+1}
-};
+// pairs p = t + 32 m of the column, in batches of BS 16-byte loads; the loads
+// of the next batch (of this column or the next) are issued before the
+// current batch is multiplied, so each warp keeps a batch in flight while it
+// computes.  Each element is split into hi + lo floats with integer
+// operations and multiplied into a double-float accumulator against the
+// split of V (shared memory), so a product costs FP32-pipe and integer
+// instructions only.  FP64 work per column (the slot correction
+// (V P) Q[l,:]^T, the conversion of the double-float sum, z = y / r) is done
+// once per CTA by one thread per column: a warp-wide FP64 instruction
+// occupies the FP64 pipe for many cycles even with one lane active.  One CTA
+// (8 warps) per walker and DF_CPB columns.
 constexpr int DF_CPB = 64;   // columns per CTA of the warp-per-column double-float accept
 
-template <bool MIXED, int NP2>
+template <int NP2>
 __global__ void __launch_bounds__(PT, 2) k_accept_delayed_warp_df(DevLayout L, DevState<double> S, DevOperand V,
                                                                    const uint8_t* mask) {
-    __shared__ __align__(16) float4 sV4[32 * NP2];   // (hi v_2p, hi v_2p+1, lo v_2p, lo v_2p+1), or VMix
+    constexpr int BS = NP2 >= 16 ? 8 : NP2 / 2;   // 16-byte loads per lane per batch
+    constexpr int NBT = NP2 / BS;                 // batches per column (even)
+    __shared__ __align__(16) float4 sV4[32 * NP2];   // (hi v_2p, hi v_2p+1, lo v_2p, lo v_2p+1)
     __shared__ double sVP[64];
+    __shared__ double sCorr[DF_CPB];
+    __shared__ float2 sY[DF_CPB];
     const int w = blockIdx.x;
     if (mask && !mask[w]) return;
     if (S.pst[w] != 0) return;
@@ -687,77 +882,74 @@ __global__ void __launch_bounds__(PT, 2) k_accept_delayed_warp_df(DevLayout L, D
     const int Kc = L.Kc, cu = S.tau[w];
     const int np = n >> 1;   // n is even
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int l0 = blockIdx.y * DF_CPB;
+    const int ncol = min(n - l0, DF_CPB);
     const double* vb = vec_ptr<double>(V, L, w, 0, n);
     for (int p = threadIdx.x; p < 32 * NP2; p += PT) {
         const double v0 = p < np ? vb[2 * p] : 0.0, v1 = p < np ? vb[2 * p + 1] : 0.0;
-        float h0, l0, h1, l1;
-        split_d(v1, h1, l1);
-        if (MIXED) {
-            VMix m;
-            m.ve = v0;
-            m.oh = h1;
-            m.ol = l1;
-            reinterpret_cast<VMix*>(sV4)[p] = m;
-        } else {
-            split_d(v0, h0, l0);
-            sV4[p] = make_float4(h0, h1, l0, l1);
-        }
+        float h0, lo0, h1, lo1;
+        split_d(v0, h0, lo0);
+        split_d(v1, h1, lo1);
+        sV4[p] = make_float4(h0, h1, lo0, lo1);
     }
     for (int c = threadIdx.x; c < cu; c += PT) sVP[c] = S.VP[(long long)w * MAXKK * Kc + c];
-    const double rinv = S.Rinv[(long long)w * MAXKK * MAXKK];
     __syncthreads();
+    if (threadIdx.x < ncol) {
+        // slot correction of column l0 + t: (V P) Q[l,:]^T, in FP64
+        const double* qrow = S.Q + (vo + l0 + threadIdx.x) * Kc;
+        double c = 0.0;
+        for (int t = 0; t < cu; ++t) c = fma(sVP[t], qrow[t], c);
+        sCorr[threadIdx.x] = c;
+    }
     const double* Gw = S.G + L.mo(w);
-    const int l_end = min(n, (int)(blockIdx.y + 1) * DF_CPB);
-    for (int l = blockIdx.y * DF_CPB + wid; l < l_end; l += PT / 32) {
-        const double2* __restrict__ c2 = reinterpret_cast<const double2*>(Gw + (long long)l * n);
-        float ah0 = 0.f, al0 = 0.f, ah1 = 0.f, al1 = 0.f;
-        double a64 = 0.0, corr = 0.0;
-        // at most 16 loads in flight per lane (n = 2048: two batches per column)
-        constexpr int NB = NP2 < 16 ? NP2 : 16;
-#pragma unroll 1
-        for (int m0 = 0; m0 < NP2; m0 += NB) {
-            double2 g[NB];
+    // this warp's columns l0 + wid + 8 i, as a flat sequence of (column, batch) items
+    const int nmine = ncol > wid ? (ncol - wid + 7) / 8 : 0;
+    const int T = nmine * NBT;
+    auto load = [&](double2 (&buf)[BS], int t) {
+        const int c = t / NBT, b = t % NBT;
+        const double2* c2 = reinterpret_cast<const double2*>(Gw + (long long)(l0 + wid + 8 * c) * n);
 #pragma unroll
-            for (int m = 0; m < NB; ++m) {
-                const int p = lane + 32 * (m0 + m);
-                g[m] = p < np ? c2[p] : make_double2(0.0, 0.0);
-            }
-            if (m0 == 0 && lane == 0) {
-                // the slot correction, in FP64, while the loads are in flight
-                const double* qrow = S.Q + (vo + l) * Kc;
-                for (int c = 0; c < cu; ++c) corr = fma(sVP[c], qrow[c], corr);
-            }
+        for (int m = 0; m < BS; ++m) {
+            const int p = lane + 32 * (b * BS + m);
+            buf[m] = p < np ? c2[p] : make_double2(0.0, 0.0);
+        }
+    };
+    float ah0 = 0.f, al0 = 0.f, ah1 = 0.f, al1 = 0.f;
+    auto compute = [&](const double2 (&buf)[BS], int t) {
+        const int b = t % NBT;
 #pragma unroll
-            for (int m = 0; m < NB; ++m) {
-                const int p = lane + 32 * (m0 + m);
-                float gh, gl;
-                if (MIXED) {
-                    const VMix v = reinterpret_cast<const VMix*>(sV4)[p];
-                    a64 = fma(v.ve, g[m].x, a64);
-                    split_d(g[m].y, gh, gl);
-                    if (m & 1) df_fma(ah1, al1, v.oh, v.ol, gh, gl);
-                    else df_fma(ah0, al0, v.oh, v.ol, gh, gl);
-                } else {
-                    const float4 v = sV4[p];
-                    split_d(g[m].x, gh, gl);
-                    df_fma(ah0, al0, v.x, v.z, gh, gl);
-                    split_d(g[m].y, gh, gl);
-                    df_fma(ah1, al1, v.y, v.w, gh, gl);
-                }
-            }
+        for (int m = 0; m < BS; ++m) {
+            const int p = lane + 32 * (b * BS + m);
+            float gh, gl;
+            const float4 v = sV4[p];
+            split_d(buf[m].x, gh, gl);
+            df_fma(ah0, al0, v.x, v.z, gh, gl);
+            split_d(buf[m].y, gh, gl);
+            df_fma(ah1, al1, v.y, v.w, gh, gl);
         }
-        if (MIXED) {
-            float h, lo;
-            split_d(a64, h, lo);
-            df_add(ah1, al1, h, lo);
+        if (b == NBT - 1) {
+            // column done: warp sum, kept as a float pair until the epilogue
+            df_add(ah0, al0, ah1, al1);
+            df_warp_sum(ah0, al0);
+            if (lane == 0) sY[wid + 8 * (t / NBT)] = make_float2(ah0, al0);
+            ah0 = al0 = ah1 = al1 = 0.f;
         }
-        df_add(ah0, al0, ah1, al1);
-        df_warp_sum(ah0, al0);
-        if (lane == 0) {
-            const double z = rinv * (df_to_double(ah0, al0) - corr);
-            S.Q[(vo + l) * Kc + cu] = z;
-            if (S.P32h) store_split(S, 1, (vo + l) * L.Kc32 + cu, z);
-        }
+    };
+    double2 buf0[BS], buf1[BS];
+    if (T > 0) load(buf0, 0);
+    for (int t = 0; t < T; t += 2) {   // T is even
+        load(buf1, t + 1);
+        compute(buf0, t);
+        if (t + 2 < T) load(buf0, t + 2);
+        compute(buf1, t + 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < ncol) {
+        const int l = l0 + threadIdx.x;
+        const float2 y2 = sY[threadIdx.x];
+        const double z = S.Rinv[(long long)w * MAXKK * MAXKK] * (df_to_double(y2.x, y2.y) - sCorr[threadIdx.x]);
+        S.Q[(vo + l) * Kc + cu] = z;
+        if (S.P32h) store_split(S, 1, (vo + l) * L.Kc32 + cu, z);
     }
 }
 
@@ -935,7 +1127,7 @@ __global__ void __launch_bounds__(256) k_flush_df(DevLayout L, DevState<double> 
             const int w = w0 + i;
             const int nt = (L.nw(w) + 31) / 32;
             const int ntl = TileIter::tiles(nt, PF);
-            for (long long t = ti.first(ntl); t < ntl; t += gridDim.x) {
+            for (int t = ti.first(ntl); t < ntl; t += gridDim.x) {
                 int tJ, tL;
                 TileIter::coords(t, nt, PF, tJ, tL);
                 flush_df_tile<PF>(L, S, w, tau, tJ, tL, sm);
@@ -1079,14 +1271,20 @@ __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int 
     T* Gw = S.G + L.mo(w);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     const int j0 = tJ * 32, l0 = tL * 32;
+    // the accumulator starts at the old value (for the determinant, -P is
+    // accumulated), so the update costs the FMAs alone
     T acc[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = s_zero(T());
+    for (int q = 0; q < 4; ++q) {
+        const int j = j0 + tx, l = l0 + ty + 8 * q;
+        acc[q] = (j < n && l < n) ? Gw[(long long)l * n + j] : s_zero(T());
+    }
     for (int c0 = 0; c0 < cu; c0 += 64) {
         for (int e = threadIdx.x; e < 32 * 64; e += 256) {
             const int r = e / 64, c = e % 64;
             const bool okc = c0 + c < cu;
-            sP[r][c] = (okc && j0 + r < n) ? S.P[(vo + j0 + r) * Kc + c0 + c] : s_zero(T());
+            const T pv = (okc && j0 + r < n) ? S.P[(vo + j0 + r) * Kc + c0 + c] : s_zero(T());
+            sP[r][c] = PF ? pv : s_neg(pv);
             sQ[r][c] = (okc && l0 + r < n) ? S.Q[(vo + l0 + r) * Kc + c0 + c] : s_zero(T());
         }
         __syncthreads();
@@ -1100,15 +1298,7 @@ __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int 
     }
     // element (j0+tx, l0+ty+8q) lives at G[(l0+ty+8q)*n + j0+tx]
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int j = j0 + tx, l = l0 + ty + 8 * q;
-        T nv = s_zero(T());
-        if (j < n && l < n) {
-            T g = Gw[(long long)l * n + j];
-            nv = PF ? (g + acc[q]) : (g - acc[q]);
-        }
-        sT[ty + 8 * q][tx] = nv;
-    }
+    for (int q = 0; q < 4; ++q) sT[ty + 8 * q][tx] = acc[q];
     __syncthreads();
     if (!PF) {
 #pragma unroll
@@ -1156,7 +1346,7 @@ __global__ void __launch_bounds__(256) k_flush_native(DevLayout L, DevState<T> S
             const int w = w0 + i;
             const int nt = (L.nw(w) + 31) / 32;
             const int ntl = TileIter::tiles(nt, PF);
-            for (long long t = ti.first(ntl); t < ntl; t += gridDim.x) {
+            for (int t = ti.first(ntl); t < ntl; t += gridDim.x) {
                 int tJ, tL;
                 TileIter::coords(t, nt, PF, tJ, tL);
                 flush_native_tile<T, PF>(L, S, w, tau, tJ, tL, sP, sQ, sT);
@@ -1333,12 +1523,38 @@ __global__ void k_commit_moves(int W, int n, int k, int* occ, const int* slot, c
 // launchers
 // ---------------------------------------------------------------------------
 template <typename T>
-void launch_propose(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& U,
-                    const DevOperand& V, const T* C, T* ratio_out, int* st_out, cudaStream_t st) {
+void launch_propose(bool pf, bool delayed, bool df, const DevLayout& L, const DevState<T>& S,
+                    const DevOperand& U_in, const DevOperand& V, const T* C, T* ratio_out, int* st_out,
+                    cudaStream_t st) {
     const size_t dyn = delayed ? (size_t)L.Kc * MAXKK * sizeof(T) : 0;
     const unsigned all = (L.kk >= 32) ? 0xffffffffu : ((1u << L.kk) - 1u);
+    DevOperand U = U_in;
     if (delayed && (U.mask & all) != all)
         k_qtu_dense<T><<<dim3(L.W, L.kk), PT, 0, st>>>(L, S, U);
+    // exactly one dense column: its pass over A^{-1} runs as its own kernel
+    const unsigned dense = ~U.mask & all;
+    if (dense != 0 && (dense & (dense - 1)) == 0) {
+        int a = 0;
+        while (!((dense >> a) & 1u)) ++a;
+        const int nr = (L.n_max + PT - 1) / PT;
+        bool launched = false;
+        if constexpr (std::is_same<T, double>::value) {
+            if (df) {
+                if (nr <= 1) k_dense_column<T, 1, true><<<L.W, PT, 0, st>>>(L, S, U, a);
+                else if (nr <= 2) k_dense_column<T, 2, true><<<L.W, PT, 0, st>>>(L, S, U, a);
+                else if (nr <= 4) k_dense_column<T, 4, true><<<L.W, PT, 0, st>>>(L, S, U, a);
+                else k_dense_column<T, 8, true><<<L.W, PT, 0, st>>>(L, S, U, a);
+                launched = true;
+            }
+        }
+        if (!launched) {
+            if (nr <= 1) k_dense_column<T, 1, false><<<L.W, PT, 0, st>>>(L, S, U, a);
+            else if (nr <= 2) k_dense_column<T, 2, false><<<L.W, PT, 0, st>>>(L, S, U, a);
+            else if (nr <= 4) k_dense_column<T, 4, false><<<L.W, PT, 0, st>>>(L, S, U, a);
+            else k_dense_column<T, 8, false><<<L.W, PT, 0, st>>>(L, S, U, a);
+        }
+        U.pre = a;
+    }
     if (!pf && !delayed) k_propose<T, false, false><<<L.W, PT, dyn, st>>>(L, S, U, V, C, ratio_out, st_out);
     if (!pf && delayed) {
         cudaFuncSetAttribute(k_propose<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -1374,9 +1590,8 @@ static void accept_npl(int npl, const DevLayout& L, const DevState<T>& S, const 
 }
 
 template <typename T>
-void launch_accept(bool pf, bool delayed, int arith, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
+void launch_accept(bool pf, bool delayed, bool df, const DevLayout& L, const DevState<T>& S, const DevOperand& V,
                    const uint8_t* mask, const int* items, int nitems, cudaStream_t st) {
-    const bool df = arith != 0;
     const int nmax = L.n_max;
     int npl = 1;
     while (32 * npl < nmax) npl *= 2;
@@ -1390,11 +1605,8 @@ void launch_accept(bool pf, bool delayed, int arith, const DevLayout& L, const D
                 // rank-1, uniform even n: one warp per column of A_0^{-1}
                 dim3 grid(L.W, (L.n_uni + DF_CPB - 1) / DF_CPB);
                 const int np2 = (L.n_uni / 2 + 31) / 32;
-#define LRU_ACC_WDF(N)                                                                        \
-    case N:                                                                                   \
-        if (arith == 2) k_accept_delayed_warp_df<true, N><<<grid, PT, 0, st>>>(L, S, V, mask); \
-        else k_accept_delayed_warp_df<false, N><<<grid, PT, 0, st>>>(L, S, V, mask);          \
-        break;
+#define LRU_ACC_WDF(N) \
+    case N: k_accept_delayed_warp_df<N><<<grid, PT, 0, st>>>(L, S, V, mask); break;
                 switch (np2 <= 4 ? 4 : (np2 <= 8 ? 8 : (np2 <= 16 ? 16 : 32))) {
                     LRU_ACC_WDF(4) LRU_ACC_WDF(8) LRU_ACC_WDF(16) LRU_ACC_WDF(32) default: break;
                 }
@@ -1416,6 +1628,12 @@ void launch_accept(bool pf, bool delayed, int arith, const DevLayout& L, const D
             // rank-1 delayed accept: one thread per column of A_0^{-1}
             dim3 grid(L.W, (L.n_uni + PT - 1) / PT);
             k_accept_delayed_lane<T><<<grid, PT, 0, st>>>(L, S, V, mask);
+            done = true;
+        }
+        if (!done && pf && !delayed) {
+            // Pfaffian: the exactly skew rank-2k update over the upper triangle
+            const int nt = (nmax + 31) / 32;
+            k_accept_pf_skew<T><<<dim3(nt * (nt + 1) / 2, L.W), 256, 0, st>>>(L, S, mask);
             done = true;
         }
         if (!done) {
@@ -1490,9 +1708,9 @@ void launch_commit_moves(int W, int n, int k, int* occ, const int* slot, const i
 #endif
 
 #define LRU_INST(T)                                                                                          \
-    template void launch_propose<T>(bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&,    \
+    template void launch_propose<T>(bool, bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&, \
                                     const DevOperand&, const T*, T*, int*, cudaStream_t);                   \
-    template void launch_accept<T>(bool, bool, int, const DevLayout&, const DevState<T>&, const DevOperand&, \
+    template void launch_accept<T>(bool, bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&, \
                                    const uint8_t*, const int*, int, cudaStream_t);                          \
     template void launch_flush_native<T>(bool, const DevLayout&, const DevState<T>&, const uint8_t*, int,   \
                                          cudaStream_t);                                                     \

@@ -40,7 +40,7 @@ struct lru_ctx {
     bool pf = false, delayed = false;
     int W = 0, kk = 0, K = 0, Kc = 0, Kc32 = 0, flush = 0;
     bool split_bf16 = false;
-    int arith = 0;               // 0 dtype arithmetic, 1 double-float, 2 mixed (F64 only)
+    bool df = false;             // double-float GEMV (F64 handles)
     int device = 0;
     cudaStream_t stream = nullptr;
     int n_uni = 0, n_max = 0;
@@ -214,7 +214,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     if (kk > MAXKK) return LRU_ERR_ARG;
     if (cfg->delay < 0) return LRU_ERR_ARG;
     if (cfg->flush < LRU_FLUSH_NATIVE || cfg->flush > LRU_FLUSH_SPLIT) return LRU_ERR_ARG;
-    if (cfg->arith < LRU_ARITH_NATIVE || cfg->arith > LRU_ARITH_MIXED) return LRU_ERR_ARG;
+    if (cfg->arith != LRU_ARITH_NATIVE && cfg->arith != LRU_ARITH_DF) return LRU_ERR_ARG;
     if (cfg->tile_chunks < 0) return LRU_ERR_ARG;
     if (cfg->refresh < LRU_REFRESH_AUTO || cfg->refresh > LRU_REFRESH_TENSOR) return LRU_ERR_ARG;
     const bool delayed = cfg->delay >= 2;
@@ -239,7 +239,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     h->Kc32 = bf16 ? (h->Kc + 63) / 64 * 64 : (h->Kc + 31) / 32 * 32;
     h->flush = cfg->flush;
     h->device = cfg->device;
-    h->arith = cfg->dtype == LRU_F64 ? cfg->arith : LRU_ARITH_NATIVE;
+    h->df = cfg->arith == LRU_ARITH_DF && cfg->dtype == LRU_F64;
 
     // geometry
     h->n_h.resize(h->W);
@@ -531,6 +531,14 @@ lru_status lru_refresh_from_scratch(lru_handle h, const void* A, const uint8_t* 
     return do_init(h, A, mask, drift, nullptr, nullptr, true);
 }
 
+// 1 if exactly one slot of the operand is dense (launch_propose then runs that
+// column's pass over A^{-1} as its own kernel), else 0
+static int one_dense_column(unsigned onehot_mask, int kk) {
+    const unsigned all = (kk >= 32) ? 0xffffffffu : ((1u << kk) - 1u);
+    const unsigned dense = ~onehot_mask & all;
+    return (dense != 0 && (dense & (dense - 1)) == 0) ? 1 : 0;
+}
+
 static bool operand_ok(const lru_operand* o, int kk) {
     if (!o) return false;
     const unsigned all = (kk >= 32) ? 0xffffffffu : ((1u << kk) - 1u);
@@ -549,10 +557,10 @@ lru_status lru_propose_det(lru_handle h, const lru_operand* U, const lru_operand
     DevOperand dV{V->dense, V->idx, V->onehot_mask, h->kk};
     DevLayout L = h->layout();
     const unsigned all = (1u << h->kk) - 1u;
-    h->launches += 1 + ((h->delayed && (dU.mask & all) != all) ? 1 : 0);
+    h->launches += 1 + ((h->delayed && (dU.mask & all) != all) ? 1 : 0) + one_dense_column(dU.mask, h->kk);
     prof_begin(h, LRU_PROF_PROPOSE);
     LRU_DISPATCH(h, {
-        launch_propose<T>(false, h->delayed, L, h->state<T>(), dU, dV, nullptr, (T*)ratio, st, h->stream);
+        launch_propose<T>(false, h->delayed, h->df, L, h->state<T>(), dU, dV, nullptr, (T*)ratio, st, h->stream);
     });
     prof_end(h, LRU_PROF_PROPOSE);
     lru_status s = cuda_check();
@@ -570,10 +578,10 @@ lru_status lru_propose_pf(lru_handle h, const lru_operand* B, const void* C, voi
     DevOperand dB{B->dense, B->idx, B->onehot_mask, h->kk};
     DevLayout L = h->layout();
     const unsigned all = (1u << h->kk) - 1u;
-    h->launches += 1 + ((h->delayed && (dB.mask & all) != all) ? 1 : 0);
+    h->launches += 1 + ((h->delayed && (dB.mask & all) != all) ? 1 : 0) + one_dense_column(dB.mask, h->kk);
     prof_begin(h, LRU_PROF_PROPOSE);
     LRU_DISPATCH(h, {
-        launch_propose<T>(true, h->delayed, L, h->state<T>(), dB, dB, (const T*)C, (T*)ratio, st, h->stream);
+        launch_propose<T>(true, h->delayed, h->df, L, h->state<T>(), dB, dB, (const T*)C, (T*)ratio, st, h->stream);
     });
     prof_end(h, LRU_PROF_PROPOSE);
     lru_status s = cuda_check();
@@ -663,7 +671,7 @@ lru_status lru_accept(lru_handle h, const uint8_t* mask) {
     h->launches += (nitems > 0 ? 1 : 0) + 1;
     prof_begin(h, LRU_PROF_ACCEPT);
     LRU_DISPATCH(h, {
-        launch_accept<T>(h->pf, h->delayed, h->arith, L, h->state<T>(), h->lastV, mask, h->d_items, nitems, h->stream);
+        launch_accept<T>(h->pf, h->delayed, h->df, L, h->state<T>(), h->lastV, mask, h->d_items, nitems, h->stream);
     });
     prof_end(h, LRU_PROF_ACCEPT);
     lru_status s = cuda_check();

@@ -30,7 +30,7 @@ _lib = C.CDLL(LIB_PATH)
 F64, C128, F32, C64 = 0, 1, 2, 3
 DET, PF = 0, 1
 FLUSH_NATIVE, FLUSH_TF32X3, FLUSH_TF32, FLUSH_BF16, FLUSH_BF16X3, FLUSH_DF, FLUSH_SPLIT = 0, 1, 2, 3, 4, 5, 6
-ARITH_NATIVE, ARITH_DF, ARITH_MIXED = 0, 1, 2
+ARITH_NATIVE, ARITH_DF = 0, 1
 REFRESH_AUTO, REFRESH_FP64, REFRESH_TENSOR = 0, 1, 2
 WALKER_OK, WALKER_SINGULAR, WALKER_NONFINITE, WALKER_BAD_INDEX = 0, 1, 2, 3
 

@@ -42,17 +42,22 @@ def test_det_accept_plain_and_delayed():
 
 def test_pf_accept_propose_and_flush():
     n, W, K = 256, 1024, 8
-    acc = bench.accept_roofline(0, "native", n, W, 0.69, HBM, pf=True)
-    assert acc["fp64_flop_per_launch"] == 6 * n * n * W            # GEMV + rank-2 update
+    acc = bench.accept_roofline(0, "native", n, W, 0.32, HBM, pf=True)
+    # exactly skew rank-2 update: 2 FMA per upper element, read the upper half, write both
+    assert acc["fp64_flop_per_launch"] == 2 * n * n * W
+    assert acc["bytes_per_launch"] == 1.5 * n * n * 8 * W
+    assert acc["bound"] == "hbm"                                   # 0.118 ms at HBM > 0.107 ms at FP64 peak
     assert acc["traffic"] is None
     pro = bench.pf_propose_roofline(n, W, 0.18, HBM)
     assert pro["bytes_per_launch"] == n * n * 8 * W and pro["fp64_flop_per_launch"] == 2 * n * n * W
     assert pro["bound"] == "alu"                                   # 0.107 ms at FP64 peak > 0.079 ms at HBM
+    prd = bench.pf_propose_roofline(n, W, 0.09, HBM, "df")        # double-float pass: FP32 pipe
+    assert prd["bound"] == "hbm" and prd["fp64_flop_per_launch"] == 0
     assert bench.pf_propose_roofline(n, W, None, HBM) is None
     fl = bench.pf_flush_roofline("native", n, W, K, 2.66, HBM)
     # upper half of A_0^{-1} (mirrored), 2K slot columns per element
     assert math.isclose(fl["flop_per_full_flush"], 2 * (n * (n + 1) / 2) * 2 * K * W)
-    assert fl["bytes_per_full_flush"] == 2 * n * n * 8 * W
+    assert fl["bytes_per_full_flush"] == 1.5 * n * n * 8 * W
     assert fl["bound"] == "alu" and math.isclose(fl["frac"], fl["achieved"] / FP64)
     fd = bench.pf_flush_roofline("df", n, W, K, 2.05, HBM)
     assert fd["bound"] == "hbm" and math.isclose(fd["frac"], fd["hbm"]["frac"])
