@@ -451,6 +451,7 @@ PF_ARMS = {
     "delayed_dfflush": (None, "native", "df"),        # FP64 propose, double-float skew flush
     "plain_dfprop": (0, "df", "native"),              # double-float pass X = A^{-1} x, skew accept
     "delayed_df": (None, "df", "df"),                 # double-float pass and flush
+    "delayed_split": (None, "native", "split"),       # FP64 propose, split-product flush + skew projection
 }
 PF_METRIC = "walker-updates/sec, Pfaffian rank-2 row-and-column moves (delayed vs plain, same GPU); roofline fraction"
 

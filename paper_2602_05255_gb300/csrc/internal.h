@@ -125,6 +125,7 @@ struct OzWork {
     int* eS;          // W x n  power-of-two exponents of the S columns
     int* eP;          // W x n  power-of-two exponents of the panel rows
     uint8_t* go;      // W      walkers that flush now (split-product flush)
+    int* cs;          // W x 64 exponent shifts of the slot columns (split-product flush)
     double* piv;      // W x n  pivots of the register panel kernel (log|det| and sign at the end)
 };
 // columns a split-product update writes: [c_lo, c_hi) minus [s_lo, s_hi), in
@@ -143,10 +144,14 @@ void launch_oz_finish(int W, int n, const OzWork& Z, const DevState<double>& S, 
                       bool reset_tau, cudaStream_t st);
 void launch_oz_drift_store(int W, int n, const DevLayout& L, const DevState<double>& S, const double* M,
                            const uint8_t* mask, double* drift, bool delayed, cudaStream_t st);
-// delayed determinant flush A_0^{-1} -= P Q^T as the same exact split product
-// (uniform n, n % 128 == 0, Kc <= 64); walkers with tau >= K, or force && tau > 0
-bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, const double* Q, const int* tau,
-                        const uint8_t* force, const OzWork& Z, int* err, cudaStream_t st);
+// delayed flush A_0^{-1} += sgnQ * P Q^T (determinant: -1, Pfaffian: +1) as the
+// same exact split product (uniform n, n % 128 == 0, Kc <= 64); walkers with
+// tau >= K, or force && tau > 0 (their go flags stay set for launch_skew_project)
+bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, const double* Q, double sgnQ,
+                        const int* tau, const uint8_t* force, const OzWork& Z, int* err, cudaStream_t st);
+// A_0^{-1} of the walkers with go[w] set := its skew part, lower triangle the
+// exact negative of the upper (after the Pfaffian split-product flush; n % 32 == 0)
+void launch_skew_project(int W, int n, double* G, const uint8_t* go, cudaStream_t st);
 // hook(ctx, class, begin) brackets the panel (class 4) and update (class 5) launches
 bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const DevState<double>& S,
                        const uint8_t* mask, bool delayed, bool reset_tau, int* err, cudaStream_t st,

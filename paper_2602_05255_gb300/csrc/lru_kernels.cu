@@ -1271,20 +1271,14 @@ __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int 
     T* Gw = S.G + L.mo(w);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     const int j0 = tJ * 32, l0 = tL * 32;
-    // the accumulator starts at the old value (for the determinant, -P is
-    // accumulated), so the update costs the FMAs alone
     T acc[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int j = j0 + tx, l = l0 + ty + 8 * q;
-        acc[q] = (j < n && l < n) ? Gw[(long long)l * n + j] : s_zero(T());
-    }
+    for (int q = 0; q < 4; ++q) acc[q] = s_zero(T());
     for (int c0 = 0; c0 < cu; c0 += 64) {
         for (int e = threadIdx.x; e < 32 * 64; e += 256) {
             const int r = e / 64, c = e % 64;
             const bool okc = c0 + c < cu;
-            const T pv = (okc && j0 + r < n) ? S.P[(vo + j0 + r) * Kc + c0 + c] : s_zero(T());
-            sP[r][c] = PF ? pv : s_neg(pv);
+            sP[r][c] = (okc && j0 + r < n) ? S.P[(vo + j0 + r) * Kc + c0 + c] : s_zero(T());
             sQ[r][c] = (okc && l0 + r < n) ? S.Q[(vo + l0 + r) * Kc + c0 + c] : s_zero(T());
         }
         __syncthreads();
@@ -1298,7 +1292,15 @@ __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int 
     }
     // element (j0+tx, l0+ty+8q) lives at G[(l0+ty+8q)*n + j0+tx]
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sT[ty + 8 * q][tx] = acc[q];
+    for (int q = 0; q < 4; ++q) {
+        const int j = j0 + tx, l = l0 + ty + 8 * q;
+        T nv = s_zero(T());
+        if (j < n && l < n) {
+            T g = Gw[(long long)l * n + j];
+            nv = PF ? (g + acc[q]) : (g - acc[q]);
+        }
+        sT[ty + 8 * q][tx] = nv;
+    }
     __syncthreads();
     if (!PF) {
 #pragma unroll

@@ -271,11 +271,12 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     if (!uniform && h->pf) { /* ragged Pfaffian handles are allowed */ }
     {
         const int n = h->n_uni;
-        const bool fits = h->dtype == LRU_F64 && !h->pf && n > 0 && n % 128 == 0 && n >= 128 && n <= 2048 &&
-                          h->W <= 65535;
+        // the split-product kernels: F64, uniform n % 128 == 0 up to 2048
+        const bool shape = h->dtype == LRU_F64 && n > 0 && n % 128 == 0 && n >= 128 && n <= 2048 && h->W <= 65535;
+        const bool fits = shape && !h->pf;   // the tensor-core refresh: determinants
         if (cfg->refresh == LRU_REFRESH_TENSOR && !fits) { delete h; return LRU_ERR_UNSUPPORTED; }
         h->oz_ok = fits && cfg->refresh != LRU_REFRESH_FP64;
-        if (cfg->flush == LRU_FLUSH_SPLIT && !(fits && delayed && h->Kc <= 64)) { delete h; return LRU_ERR_UNSUPPORTED; }
+        if (cfg->flush == LRU_FLUSH_SPLIT && !(shape && delayed && h->Kc <= 64)) { delete h; return LRU_ERR_UNSUPPORTED; }
     }
 
     if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); delete h; return LRU_ERR_CUDA; }
@@ -640,11 +641,17 @@ static lru_status do_flush(lru_handle h, const uint8_t* force) {
         OzWork Z{};
         oz_work_carve(Z, h->ozw, h->W, h->n_uni);
         Z.M = (double*)h->G;
-        h->launches += 2;
+        h->launches += 4;   // flush flags, column balance, two slicings, GEMM (+ finish counted above)
+        // determinant: A_0^{-1} -= P Q^T (Eq. delayed_Ainv); Pfaffian: A_0^{-1} += P Q^T
+        // (Eq. pf_delayed_Ainv), then projected back onto an exactly skew matrix
         if (!launch_flush_split(h->W, h->n_uni, h->K, h->Kc, h->kk, (const double*)h->P, (const double*)h->Q,
-                                h->tau, force, Z, h->err, h->stream)) {
+                                h->pf ? 1.0 : -1.0, h->tau, force, Z, h->err, h->stream)) {
             prof_end(h, LRU_PROF_FLUSH);
             return LRU_ERR_UNSUPPORTED;
+        }
+        if (h->pf) {
+            launch_skew_project(h->W, h->n_uni, (double*)h->G, Z.go, h->stream);
+            h->launches += 1;
         }
     } else if (h->flush == LRU_FLUSH_DF) {
         launch_flush_df(h->pf, L, h->state<double>(), force, h->stream);

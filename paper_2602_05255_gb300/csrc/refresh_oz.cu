@@ -339,20 +339,58 @@ __global__ void k_oz_flush_go(int W, int K, const int* tau, const uint8_t* force
     go[w] = (force ? (force[w] && t > 0) : (t >= K)) ? 1 : 0;
 }
 
+// Column balance of the slot matrices before they are sliced.  Every row is
+// written as digits of one power-of-two scale (its largest entry), so a slot
+// column much larger than the others (the step of a near-node update) would
+// cost the other entries of the row their low bits.  Column c of P is scaled
+// by 2^s_c and column c of Q by 2^-s_c, with s_c half the exponent gap of the
+// two columns' maxima: P Q^T is unchanged exactly (powers of two), and the
+// entries of a row span a far smaller range.  Persistent over walkers.
+__global__ void __launch_bounds__(256) k_oz_col_balance(int W, int n, int ldx, int kk, const double* P,
+                                                        const double* Q, const int* tau, const uint8_t* go,
+                                                        int* cs) {
+    __shared__ int sp[4][OZ_B], sq[4][OZ_B];
+    const int c = threadIdx.x % OZ_B, g = threadIdx.x / OZ_B;   // 64 columns x 4 row groups
+    for (int w = blockIdx.x; w < W; w += gridDim.x) {
+        if (!go[w]) continue;
+        const int cu = tau[w] * kk;
+        int ep = 0, eq = 0;
+        if (c < cu)
+            for (int r = g; r < n; r += 4) {
+                ep = max(ep, oz_bexp(P[((long long)w * n + r) * ldx + c]));
+                eq = max(eq, oz_bexp(Q[((long long)w * n + r) * ldx + c]));
+            }
+        sp[g][c] = ep;
+        sq[g][c] = eq;
+        __syncthreads();
+        if (g == 0) {
+            ep = max(max(sp[0][c], sp[1][c]), max(sp[2][c], sp[3][c]));
+            eq = max(max(sq[0][c], sq[1][c]), max(sq[2][c], sq[3][c]));
+            cs[(long long)w * OZ_B + c] = (ep > 0 && eq > 0) ? (eq - ep) / 2 : 0;
+        }
+        __syncthreads();
+    }
+}
+
 // Rows of the walkers' slot matrices X (rows of ldx doubles): the cu =
-// tau * kk filled slot columns times sgn, zeros after; slices and exponent as
-// for the panel rows.  Persistent over walkers: on steps where no walker
-// flushes every block leaves after reading the go flags.
+// tau * kk filled slot columns times sgn * 2^(cdir * cs[c]) (the column
+// balance, exact), zeros after; slices and exponent as for the panel rows.
+// Persistent over walkers: on steps where no walker flushes every block
+// leaves after reading the go flags.
+__device__ __forceinline__ double oz_pow2(int k) { return __hiloint2double((1023 + k) << 20, 0); }
 __global__ void __launch_bounds__(256) k_oz_slice_rows(int W, int n, int ldx, int kk, const double* X, double sgn,
-                                                       const int* tau, const uint8_t* go, uint16_t* dst, int* ex) {
+                                                       const int* cs, int cdir, const int* tau, const uint8_t* go,
+                                                       uint16_t* dst, int* ex) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int w = blockIdx.x; w < W; w += gridDim.x) {
         if (!go[w]) continue;
         const int cu = tau[w] * kk;
+        const double fa = lane < cu ? sgn * oz_pow2(cdir * cs[(long long)w * OZ_B + lane]) : 0.0;
+        const double fb = lane + 32 < cu ? sgn * oz_pow2(cdir * cs[(long long)w * OZ_B + lane + 32]) : 0.0;
         for (int r = wid; r < n; r += 8) {
             const double* row = X + ((long long)w * n + r) * ldx;
-            const double a = lane < cu ? sgn * row[lane] : 0.0;
-            const double b = lane + 32 < cu ? sgn * row[lane + 32] : 0.0;
+            const double a = lane < cu ? fa * row[lane] : 0.0;
+            const double b = lane + 32 < cu ? fb * row[lane + 32] : 0.0;
             const int mx = __reduce_max_sync(0xffffffffu, max(oz_bexp(a), oz_bexp(b)));
             const int E = mx > 0 ? mx - 1022 : 0;
             uint16_t ha[OZ_S], hb[OZ_S];
@@ -385,6 +423,7 @@ size_t oz_work_bytes(int W, int n) {
     take(Wn * sizeof(int));                        // eP
     take((size_t)W);                               // go
     take(Wn * sizeof(double));                     // piv
+    take((size_t)W * OZ_B * sizeof(int));          // cs
     return b;
 }
 
@@ -402,6 +441,7 @@ void oz_work_carve(OzWork& Z, void* base, int W, int n) {
     Z.eP = (int*)take(Wn * sizeof(int));
     Z.go = (uint8_t*)take((size_t)W);
     Z.piv = (double*)take(Wn * sizeof(double));
+    Z.cs = (int*)take((size_t)W * OZ_B * sizeof(int));
 }
 
 // rows x 64 BF16 matrix, box 64 x box_rows, SWIZZLE_128B
@@ -471,8 +511,8 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
 // with M = the stored A_0^{-1} (row l of storage = column l of A_0^{-1}),
 // M[l][j] += sum_c (-Q)[l][c] P[j][c]: the P rows take the place of the S
 // columns, the -Q rows that of the panel rows, no column is skipped.
-bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, const double* Q, const int* tau,
-                        const uint8_t* force, const OzWork& Z, int* err, cudaStream_t st) {
+bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, const double* Q, double sgnQ,
+                        const int* tau, const uint8_t* force, const OzWork& Z, int* err, cudaStream_t st) {
     if (Kc < 1 || Kc > OZ_B) return false;
     const long long rows = (long long)W * OZ_S * n;
     if (rows >= (1ll << 31)) return false;
@@ -502,8 +542,9 @@ bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, co
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     k_oz_flush_go<<<(W + 255) / 256, 256, 0, st>>>(W, K, tau, force, Z.go);
     const int sgrid = std::min(W, 8 * nsm);
-    k_oz_slice_rows<<<sgrid, 256, 0, st>>>(W, n, Kc, kk, P, 1.0, tau, Z.go, Z.Sb, Z.eS);
-    k_oz_slice_rows<<<sgrid, 256, 0, st>>>(W, n, Kc, kk, Q, -1.0, tau, Z.go, Z.Pb, Z.eP);
+    k_oz_col_balance<<<sgrid, 256, 0, st>>>(W, n, Kc, kk, P, Q, tau, Z.go, Z.cs);
+    k_oz_slice_rows<<<sgrid, 256, 0, st>>>(W, n, Kc, kk, P, 1.0, Z.cs, 1, tau, Z.go, Z.Sb, Z.eS);
+    k_oz_slice_rows<<<sgrid, 256, 0, st>>>(W, n, Kc, kk, Q, sgnQ, Z.cs, -1, tau, Z.go, Z.Pb, Z.eP);
     auto kern = k_oz_gemm<1>;
     switch ((Kc + 15) / 16) {
         case 2: kern = k_oz_gemm<2>; break;
@@ -514,6 +555,50 @@ bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, co
     const OzCols all{0, n, -1, -1, 0, n / OZ_TJ};
     kern<<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, all, Z, Z.go, err);
     return true;
+}
+
+// Projection of the flushed walkers' A_0^{-1} onto its skew part, after the
+// Pfaffian split-product flush A_0^{-1} += P Q^T: the exact products of the
+// rounded slots (P = a M^{-1}, Q = a) are skew only up to that rounding, and
+// the upper entry becomes (G_jl - G_lj) / 2, the lower one its exact negative
+// (sign flip), the diagonal zero.  One CTA per (walker, 32 x 32 upper tile).
+__global__ void __launch_bounds__(256) k_skew_project(int n, double* G, const uint8_t* go) {
+    __shared__ double sU[32][33], sL[32][33];
+    const int w = blockIdx.y;
+    if (!go[w]) return;
+    const int nt = n / 32;
+    int r = 0, rem = (int)blockIdx.x;
+    while (rem >= nt - r) { rem -= nt - r; ++r; }
+    const int j0 = 32 * r, l0 = 32 * (r + rem);
+    double* Gw = G + (long long)w * n * n;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    // sU[l][j] = G(j0 + j, l0 + l) at Gw[l * n + j]; sL[j][l] = G(l0 + l, j0 + j) at Gw[j * n + l]
+    for (int q = 0; q < 4; ++q) {
+        const int a = ty + 8 * q;
+        sU[a][tx] = Gw[(long long)(l0 + a) * n + j0 + tx];
+        sL[a][tx] = Gw[(long long)(j0 + a) * n + l0 + tx];
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+        const int a = ty + 8 * q;   // l within the tile, tx = j
+        double v;
+        if (r == r + rem && tx == a) v = 0.0;
+        else if (r == r + rem && tx > a) v = -0.5 * (sU[tx][a] - sL[a][tx]);   // below the diagonal
+        else v = 0.5 * (sU[a][tx] - sL[tx][a]);
+        Gw[(long long)(l0 + a) * n + j0 + tx] = v;
+    }
+    if (rem != 0)
+        for (int q = 0; q < 4; ++q) {
+            const int a = ty + 8 * q;   // j within the tile, tx = l
+            const double v = 0.5 * (sU[tx][a] - sL[a][tx]);
+            Gw[(long long)(j0 + a) * n + l0 + tx] = __hiloint2double(__double2hiint(v) ^ (int)0x80000000,
+                                                                      __double2loint(v));
+        }
+}
+
+void launch_skew_project(int W, int n, double* G, const uint8_t* go, cudaStream_t st) {
+    const int nt = n / 32;
+    k_skew_project<<<dim3(nt * (nt + 1) / 2, W), 256, 0, st>>>(n, G, go);
 }
 
 }  // namespace lru

@@ -88,16 +88,19 @@ def test_tensor_flush_needs_delayed_f64(lib):
 
 
 def test_split_flush_and_tensor_refresh_shapes(lib):
-    # the exact split-product flush: delayed F64 determinants, uniform n % 128 == 0,
-    # n <= 2048, K * k <= 64; the tensor-core refresh: F64 determinants, same n rule
+    # the exact split-product flush: delayed F64 handles, uniform n % 128 == 0,
+    # n <= 2048, K * k <= 64 (Pfaffian K * 2k); the tensor-core refresh: F64
+    # determinants, same n rule
     base = dict(kind=0, dtype=0, walkers=4, n=256, n_per_walker=None, k=1, k_per_walker=None, delay=8,
                 flush=6, device=0)
     h = ctypes.c_void_p()
-    for field, value in [("n", 200), ("n", 4096), ("dtype", 1), ("kind", 1), ("delay", 0), ("delay", 65)]:
+    for field, value in [("n", 200), ("n", 4096), ("dtype", 1), ("delay", 0), ("delay", 65)]:
         cfg = Cfg(**base)
         setattr(cfg, field, value)
         code = lib.lru_create(ctypes.byref(cfg), ctypes.byref(h))
         assert code in (1, 8) and not h.value, (field, value, code)   # invalid, or not supported
+    cfg = Cfg(**{**base, "kind": 1, "delay": 33})                      # Pfaffian: 33 x 2 slot columns > 64
+    assert lib.lru_create(ctypes.byref(cfg), ctypes.byref(h)) == 1 and not h.value
     for field, value in [("n", 200), ("dtype", 1), ("kind", 1)]:
         cfg = Cfg(**{**base, "flush": 0, "delay": 0})
         cfg.refresh = 2

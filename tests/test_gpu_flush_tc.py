@@ -121,12 +121,12 @@ def test_det_rank2_two_k_chunks():
     assert (st.tau().cpu().numpy() == steps % K).all()
 
 
-@pytest.mark.parametrize("flush", [1, 5])
+@pytest.mark.parametrize("flush", [1, 5, 6])
 def test_pf_delayed_flush_exactly_skew(flush):
     # realistic pairing chain: the flushed A_0^{-1} is exactly skew in both
     # precisions; the double-float flush also meets the FP64 bar (64x roundoff)
     L = lrugb()
-    W, n, m, steps, K = 4, 136, 300, 16, 8
+    W, n, m, steps, K = 4, 256 if flush == 6 else 136, 512 if flush == 6 else 300, 16, 8
     F, pos0, slot, new = pf_workload(421, W, n, m, steps)
     st = L.LowRankState("pf", W, n, k=1, dtype=torch.float64, delay=K, flush=flush)
     F_d, pos_d = tdev(F), tdev(pos0)
@@ -143,7 +143,7 @@ def test_pf_delayed_flush_exactly_skew(flush):
     inv = st.inverse().cpu().numpy()      # = A_0^{-1} right after the second flush
     for w in range(W):
         assert np.array_equal(inv[w], -inv[w].T)
-        if flush != 5:
+        if flush == 1:
             continue
         pos = pos0[w].copy()
         car = O.init_pf_carrier(O.pairing_matrix(F, pos), K)
@@ -153,8 +153,9 @@ def test_pf_delayed_flush_exactly_skew(flush):
             exact.append(O.pf_ratio_direct(O.pairing_matrix(F, pos), B, C))
             chain.append(O.pf_lru_delayed(car, B, C))
             pos[slot[s, w]] = new[s, w]
-        check_ratios(ratios[:, w], chain, exact, what=w, eps_scale=256.0, ceiling=CEIL_CHAIN * 256.0)
-        assert fro_rel(inv[w], O.inv(O.pairing_matrix(F, pos))) <= 256e-10
+        scale = 256.0 if flush == 5 else 1.0     # double-float flush; the split product rounds as FP64
+        check_ratios(ratios[:, w], chain, exact, what=(flush, w), eps_scale=scale, ceiling=CEIL_CHAIN * scale)
+        assert fro_rel(inv[w], O.inv(O.pairing_matrix(F, pos))) <= 1e-10 * scale
 
 
 @pytest.mark.parametrize("mode", [1, 2, 3, 4])
@@ -254,16 +255,32 @@ def test_split_flush_rejects_unsupported_shapes():
     L = lrugb()
     with pytest.raises(L.LRUError):   # n not a multiple of 128
         L.LowRankState("det", 2, 200, k=1, dtype=torch.float64, delay=8, flush=L.FLUSH_SPLIT)
-    with pytest.raises(L.LRUError):   # Pfaffian
-        L.LowRankState("pf", 2, 256, k=1, dtype=torch.float64, delay=8, flush=L.FLUSH_SPLIT)
+    with pytest.raises(L.LRUError):   # Pfaffian, n not a multiple of 128
+        L.LowRankState("pf", 2, 200, k=1, dtype=torch.float64, delay=8, flush=L.FLUSH_SPLIT)
+    with pytest.raises(L.LRUError):   # complex
+        L.LowRankState("pf", 2, 256, k=1, dtype=torch.complex128, delay=8, flush=L.FLUSH_SPLIT)
+
+
+def _column_balance(P, Q):
+    """The flush's exact column balance: column c of P times 2^s_c and of Q
+    times 2^-s_c, s_c = (eQ_c - eP_c) / 2 truncated, eX_c the biased exponent
+    of the column's largest entry (the product P Q^T is unchanged)."""
+    def bexp(x):
+        m = np.abs(x).max(0)
+        return np.where(m > 0, np.frexp(m)[1] + 1022, 0)
+    ep, eq = bexp(P), bexp(Q)
+    s = np.where((ep > 0) & (eq > 0), np.trunc((eq - ep) / 2), 0).astype(int)
+    return P * 2.0 ** s, Q * 2.0 ** -s
 
 
 def test_split_flush_against_exact_rational_arithmetic():
     # A_0^{-1} -= P Q^T on planted slots with a wide dynamic range across slot
     # columns, against exact rational arithmetic.  The split product's error
-    # bound is relative to the row maxima: |err| <= 2^-52 (maxP_j sum|Q_l| +
-    # sum|P_j| maxQ_l) + 2^-52 |result| (quantisation to 2^-56 of the maxima,
-    # levels kept down to 2^-66, two FP64 roundings).
+    # bound is relative to the row maxima of the column-balanced slots P~, Q~:
+    # |err| <= 2^-52 (maxP~_j sum|Q~_l| + sum|P~_j| maxQ~_l) + 2^-52 |result|
+    # (quantisation to 2^-56 of the maxima, levels kept down to 2^-66, two
+    # FP64 roundings).  The balance brings that bound to within a small factor
+    # of an FP64 flush's, 2^-52 (K sum_c |P_jc Q_lc| + |result|).
     from fractions import Fraction
     L = lrugb()
     W, n, K = 2, 128, 16
@@ -286,14 +303,19 @@ def test_split_flush_against_exact_rational_arithmetic():
     st.load(tdev(buf))
     st.flush(tdev(np.ones(W, np.uint8)))
     G1 = st.save().cpu().numpy()[oG:oG + W * n * n * 8].view(np.float64).reshape(W, n, n)
-    worst = 0.0
+    worst, worst64 = 0.0, 0.0
     for w in range(W):
+        Pb, Qb = _column_balance(P[w], Q[w])
         for _ in range(1500):
             l, j = g.integers(0, n, 2)          # storage row l, column j: (A^{-1})_{jl}
             ex = Fraction(G0[w, l, j]) - sum(Fraction(P[w, j, c]) * Fraction(Q[w, l, c]) for c in range(K))
-            bound = 2.0 ** -52 * (np.abs(P[w, j]).max() * np.abs(Q[w, l]).sum() +
-                                  np.abs(P[w, j]).sum() * np.abs(Q[w, l]).max() + abs(float(ex)))
+            bound = 2.0 ** -52 * (np.abs(Pb[j]).max() * np.abs(Qb[l]).sum() +
+                                  np.abs(Pb[j]).sum() * np.abs(Qb[l]).max() + abs(float(ex)))
             err = abs(float(Fraction(G1[w, l, j]) - ex))
             worst = max(worst, err / bound)
+            fp64 = 2.0 ** -52 * (K * np.abs(P[w, j] * Q[w, l]).sum() + abs(float(ex)))
+            worst64 = max(worst64, err / fp64)
+    print("split flush: worst error / own bound %.3f, / FP64 bound %.3f" % (worst, worst64))
     assert worst <= 1.0, worst
+    assert worst64 <= 8.0, worst64
     assert (st.tau().cpu().numpy() == 0).all()

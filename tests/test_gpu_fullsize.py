@@ -40,8 +40,8 @@ DF_SCALE = 256.0
 # FP64 and the double-float skew flushes, and the plain form (skew rank-2
 # accept), in FP64 and complex128; arith 1 takes the propose's pass over
 # A^{-1} in double-float arithmetic
-PF_CASES = [("f64", 8, 0, 0), ("f64", 8, 5, 0), ("c128", 8, 0, 0), ("f64", 0, 0, 0), ("c128", 0, 0, 0),
-            ("f64", 8, 5, 1), ("f64", 0, 0, 1)]
+PF_CASES = [("f64", 8, 0, 0), ("f64", 8, 5, 0), ("f64", 8, 6, 0), ("c128", 8, 0, 0), ("f64", 0, 0, 0),
+            ("c128", 0, 0, 0), ("f64", 8, 5, 1), ("f64", 0, 0, 1)]
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -138,8 +138,10 @@ def test_det_headline_1024_walkers_n1024():
         inv_chain = O.carrier_inverse(car)
         for arith, (rs, inv) in got.items():
             scale = DF_SCALE if arith == L.ARITH_DF else 1.0
+            # at n = 1024 the oracle's own chain reaches 2e-8 against the exact
+            # ratio (walker 1023): the ceiling of the bar is the headline target
             out = check_ratios(rs[:, q], chain, exact, what=("headline", arith, w), eps_scale=scale,
-                               refresh_every=every, ceiling=CEIL_CHAIN * scale)
+                               refresh_every=every, ceiling=1e-6 * scale)
             # the headline target: ratio error against the exact ratio within 1e-6
             assert out["max_err_vs_exact"] <= 1e-6
             assert fro_rel(inv[q], inv_exact) <= max(1e-10, 10 * scale * fro_rel(inv_chain, inv_exact))
