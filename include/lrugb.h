@@ -179,7 +179,9 @@ lru_status lru_propose_det(lru_handle h, const lru_operand* U, const lru_operand
                            void* ratio, int32_t* st);
 /* Pfaffian proposal (Sec. 3.1 / App. A.2; delayed: Sec. 3.3).  C: W matrices
  * of size 2k x 2k (skew, invertible), or NULL for C = -J (the paper's form,
- * A' = A - B J B^T).  ratio = pf(C^{-1} + B^T A^{-1} B) / pf(C^{-1}). */
+ * A' = A - B J B^T).  Walker w's C starts at element w * (2 kmax)^2 and is
+ * stored row-major as 2k_w x 2k_w (with uniform k: W consecutive 2k x 2k
+ * matrices).  ratio = pf(C^{-1} + B^T A^{-1} B) / pf(C^{-1}). */
 lru_status lru_propose_pf(lru_handle h, const lru_operand* B, const void* C,
                           void* ratio, int32_t* st);
 /* Applies the last proposal to the walkers with mask[w] != 0 (NULL = all)
@@ -195,8 +197,13 @@ lru_status lru_accept(lru_handle h, const uint8_t* mask);
  * accept pass.  Acceptance: walkers whose proposal status is OK and, when
  * given, mask[w] != 0 and |ratio|^2 >= u[w] (u: W doubles, Metropolis
  * uniforms).  acc_out (W uint8, may be NULL) receives the decisions.  Plain
- * (non-delayed) handles.  The call issues only a memset and one kernel on the
- * handle's stream (no allocation, no synchronisation), so it can be captured
+ * and delayed handles: in the delayed form (Sec. 2.3 / 3.3) the accept pass
+ * stores the walker's new slot and advances its own delay counter tau, and
+ * the same launch folds the slots of every walker whose tau reached K into
+ * A_0^{-1} (Eqs. delayed_Ainv, pf_delayed_Ainv) in FP64 / complex128 tiles,
+ * whatever the handle's flush precision, and resets its tau; walkers with
+ * fewer accepted moves keep their slots.  The call issues only a memset and
+ * one kernel on the handle's stream (no allocation, no synchronisation), so it can be captured
  * in a CUDA graph; make one call before capturing so that one-time kernel
  * set-up happens outside the capture.  ratio/st as in lru_propose_det; U, V
  * (det) or B (pf, with C or NULL) as in the propose calls. */

@@ -19,10 +19,15 @@ FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxe
 # (source, object, extra defines): the kernel file is split by dtype
 UNITS = [
     ("lrugb_api.cu", "lrugb_api.o", []),
-    ("lru_kernels.cu", "lru_kernels_f64.o", ["-DLRU_INST_DTYPE=double", "-DLRU_INST_PRIMARY"]),
-    ("lru_kernels.cu", "lru_kernels_c128.o", ["-DLRU_INST_DTYPE=c128"]),
-    ("lru_kernels.cu", "lru_kernels_f32.o", ["-DLRU_INST_DTYPE=float"]),
-    ("lru_kernels.cu", "lru_kernels_c64.o", ["-DLRU_INST_DTYPE=c64"]),
+    ("lru_kernels.cu", "lru_kernels_f64.o", ["-DLRU_INST_DTYPE=double", "-DLRU_INST_PRIMARY", "-DLRU_NO_STEP"]),
+    ("lru_kernels.cu", "lru_kernels_c128.o", ["-DLRU_INST_DTYPE=c128", "-DLRU_NO_STEP"]),
+    ("lru_kernels.cu", "lru_kernels_f32.o", ["-DLRU_INST_DTYPE=float", "-DLRU_NO_STEP"]),
+    ("lru_kernels.cu", "lru_kernels_c64.o", ["-DLRU_INST_DTYPE=c64", "-DLRU_NO_STEP"]),
+    # the persistent fused step, per dtype
+    ("lru_kernels.cu", "lru_step_f64.o", ["-DLRU_INST_DTYPE=double", "-DLRU_STEP_ONLY"]),
+    ("lru_kernels.cu", "lru_step_c128.o", ["-DLRU_INST_DTYPE=c128", "-DLRU_STEP_ONLY"]),
+    ("lru_kernels.cu", "lru_step_f32.o", ["-DLRU_INST_DTYPE=float", "-DLRU_STEP_ONLY"]),
+    ("lru_kernels.cu", "lru_step_c64.o", ["-DLRU_INST_DTYPE=c64", "-DLRU_STEP_ONLY"]),
     ("refresh.cu", "refresh.o", []),
     ("refresh_oz.cu", "refresh_oz.o", []),
     ("flush_tc.cu", "flush_tc.o", []),

@@ -1,13 +1,23 @@
-"""Autotuner for the delayed update: delay K and accept-pass tile.
+"""Autotuner for the delayed update: delay K, flush kernel and accept tile.
 
 The paper leaves the delay bound T to the user ("typically T ~ n/10k" for
 determinants, Sec. 2.3, and n/20k for Pfaffians, Sec. 3.3; Sec. 4.2 finds the
 best T by experiment).  This module does that experiment on the GPU: for a
-given (kind, n, k, dtype, flush precision) it times short synthetic chains of
-one-hot row (det) or row-and-column (pf) moves through the C-ABI with CUDA
-events, for delay candidates around the paper's heuristic and for several
-accept-pass tiles (columns of A^{-1} per CTA work item), and returns the
-fastest setting.  Results are cached in a JSON file keyed by the device name.
+given (kind, n, k, dtype) it times short synthetic chains of one-hot row (det)
+or row-and-column (pf) moves through the C-ABI with CUDA events, for
+
+  * delay candidates around the paper's heuristic (and the plain form),
+  * the flush kernels that keep FP64-class accuracy, each with its own tiling:
+    FP64 tiles of 32 x 32 on the CUDA cores, the exact split product on the
+    tensor cores (128 x 64 tiles of BF16 slices; F64, n % 128 == 0), and
+    double-float tiles on the FP32 pipe (F64),
+  * the GEMV arithmetic (FP64 or double-float, F64 rank-1),
+  * accept-pass tiles (columns of A^{-1} per CTA work item) for the best of
+    those,
+
+and returns the fastest setting.  Reduced-precision flushes (TF32, BF16) are
+left out unless asked for: they change the results, not just the speed.
+Results are cached in a JSON file keyed by the device name.
 """
 from __future__ import annotations
 
@@ -88,13 +98,30 @@ def _time_chain(kind, n, k, dtype, delay, flush, arith, tile, walkers, steps, se
     return walkers * (steps - warm) / (ms / 1e3)
 
 
-def tune(kind: str, n: int, k: int, dtype=torch.float64, flush: int = L.FLUSH_NATIVE, arith: int = L.ARITH_NATIVE,
-         walkers: Optional[int] = None, steps: Optional[int] = None, delays: Optional[Iterable[int]] = None,
-         tiles: Iterable[int] = (16, 32, 64, 128), use_cache: bool = True) -> Dict:
-    """Best {delay, tile_chunks, updates_per_s} for the workload; every measured
-    setting is kept under 'trials'."""
+def flush_candidates(kind: str, n: int, k: int, dtype) -> list:
+    """Flush kernels that keep FP64-class results for this shape."""
+    out = [L.FLUSH_NATIVE]
+    if dtype == torch.float64:
+        if n % 128 == 0 and 128 <= n <= 2048:
+            out.append(L.FLUSH_SPLIT)
+        out.append(L.FLUSH_DF)
+    return out
+
+
+def tune(kind: str, n: int, k: int, dtype=torch.float64, flushes: Optional[Iterable[int]] = None,
+         ariths: Optional[Iterable[int]] = None, walkers: Optional[int] = None, steps: Optional[int] = None,
+         delays: Optional[Iterable[int]] = None, tiles: Iterable[int] = (16, 32, 64, 128),
+         include_plain: bool = True, use_cache: bool = True) -> Dict:
+    """Best {delay, flush, arith, tile_chunks, updates_per_s} for the workload;
+    every measured setting is kept under 'trials'.  delay 0 is the plain form
+    (left out with include_plain=False)."""
     dev = torch.cuda.get_device_name()
-    key = f"{dev}|{kind}|n{n}|k{k}|{str(dtype)}|flush{flush}|arith{arith}"
+    flushes = list(flushes) if flushes is not None else flush_candidates(kind, n, k, dtype)
+    if ariths is None:
+        ariths = [L.ARITH_NATIVE] + ([L.ARITH_DF] if dtype == torch.float64 else [])
+    ariths = list(ariths)
+    key = (f"{dev}|{kind}|n{n}|k{k}|{str(dtype)}|flush{','.join(map(str, flushes))}|"
+           f"arith{','.join(map(str, ariths))}|plain{int(include_plain)}")
     cache = {}
     if use_cache and os.path.exists(CACHE):
         try:
@@ -105,12 +132,27 @@ def tune(kind: str, n: int, k: int, dtype=torch.float64, flush: int = L.FLUSH_NA
             return cache[key]
     walkers = walkers or max(8, min(1024, (1 << 31) // (n * n * 16)))
     delays = list(delays) if delays is not None else candidates(kind, n, k)
+    steps_ = steps or max(2 * max(delays) + 4, 24)
+    tiles = list(tiles)
     trials = []
+    # delay x flush x arithmetic at the default accept tile, then the tiles of the best
+    for arith in ariths:
+        if include_plain:
+            trials.append({"delay": 0, "flush": L.FLUSH_NATIVE, "arith": arith, "tile_chunks": 0,
+                           "updates_per_s": _time_chain(kind, n, k, dtype, 0, L.FLUSH_NATIVE, arith, 0, walkers,
+                                                        steps_)})
+        for K in delays:
+            for fl in flushes:
+                try:
+                    rate = _time_chain(kind, n, k, dtype, K, fl, arith, 0, walkers, steps_)
+                except L.LRUError:
+                    continue   # combination not built for this shape
+                trials.append({"delay": K, "flush": fl, "arith": arith, "tile_chunks": 0, "updates_per_s": rate})
+    best = max(trials, key=lambda d: d["updates_per_s"])
     for t in tiles:
-        for K in [0] + delays:
-            steps_ = steps or max(2 * max(delays) + 4, 24)
-            rate = _time_chain(kind, n, k, dtype, K, flush if K >= 2 else L.FLUSH_NATIVE, arith, t, walkers, steps_)
-            trials.append({"delay": K, "tile_chunks": t, "updates_per_s": rate})
+        rate = _time_chain(kind, n, k, dtype, best["delay"], best["flush"], best["arith"], t, walkers, steps_)
+        trials.append({"delay": best["delay"], "flush": best["flush"], "arith": best["arith"], "tile_chunks": t,
+                       "updates_per_s": rate})
     best = max(trials, key=lambda d: d["updates_per_s"])
     res = dict(best)
     res["heuristic_delay"] = heuristic_delay(kind, n, k)
@@ -121,3 +163,12 @@ def tune(kind: str, n: int, k: int, dtype=torch.float64, flush: int = L.FLUSH_NA
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)
         json.dump(cache, open(CACHE, "w"), indent=1)
     return res
+
+
+def make_state(kind: str, walkers: int, n: int, k: int = 1, dtype=torch.float64, tuned: Optional[Dict] = None,
+               **kw) -> "L.LowRankState":
+    """A LowRankState configured with a tune() result (delay, flush, GEMV
+    arithmetic, accept tile); tuned=None runs tune() first."""
+    tuned = tuned or tune(kind, n, k, dtype)
+    return L.LowRankState(kind, walkers, n, k=k, dtype=dtype, delay=tuned["delay"], flush=tuned["flush"],
+                          arith=tuned["arith"], tile_chunks=tuned["tile_chunks"], **kw)

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(AT) k_backward(DevLayout L, DevState<T> S, Dev
         }
         if (gAw)
             for (long long e = threadIdx.x; e < (long long)n * n; e += AT) gAw[e] = s_zero(T());
-        if (gC && threadIdx.x < kk * kk) gC[(long long)w * kk * kk + threadIdx.x] = s_zero(T());
+        if (gC && threadIdx.x < kk * kk) gC[(long long)w * L.kk * L.kk + threadIdx.x] = s_zero(T());
         return;
     }
     const T gw = g[w];
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(AT) k_backward(DevLayout L, DevState<T> S, Dev
             for (int a = 0; a < m; ++a)
                 for (int b = 0; b < m; ++b) {
                     double v = (b == a + m / 2) ? -1.0 : ((a == b + m / 2) ? 1.0 : 0.0);   // -J
-                    Cm[a * AMAXKK + b] = C ? C[(long long)w * m * m + a * m + b] : make_real<T>(v);
+                    Cm[a * AMAXKK + b] = C ? C[(long long)w * L.kk * L.kk + a * m + b] : make_real<T>(v);
                 }
             // C^{-1} by Gauss-Jordan on a copy (small, m <= 16)
             for (int a = 0; a < m; ++a)
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(AT) k_backward(DevLayout L, DevState<T> S, Dev
                     for (int c = 0; c < m; ++c) s = s_fma(sR[a * AMAXKK + c] - Cm[a * AMAXKK + c], Ci[c * AMAXKK + b], s);
                     T1[a * AMAXKK + b] = s;
                 }
-            T* gCw = gC + (long long)w * m * m;
+            T* gCw = gC + (long long)w * L.kk * L.kk;
             for (int a = 0; a < m; ++a)
                 for (int b = 0; b < m; ++b) {
                     // unconstrained gradient entry (a, b) = -[C^{-1} T1]_{b a} / 2

@@ -69,11 +69,16 @@ struct StepCtl {
     int* counter;             // work-queue head, zeroed before each launch
     int* prop_done;           // W flags, zeroed before each launch
     int* items_done;          // W counters, zeroed before each launch
+    int* fin;                 // W flags: the walker's propose, accept and commit are done (zeroed)
+    int* flush_done;          // W counters of finished flush strips (zeroed)
     uint8_t* acc;             // W accept decisions (output)
     const int* order;         // W walkers in propose order
     const int4* acc_items;    // accept items (walker, l0, l1, use_smem), largest walkers first
     const int* nacc_w;        // accept items per walker
     int nacc;
+    const int2* flush_items;  // delayed form: flush strips (walker, 32-column block), largest walkers first
+    const int* nflush_w;      // flush strips per walker
+    int nflush;
     int do_accept;            // 0: propose only
     const uint8_t* mask;      // optional acceptance mask
     const double* u;          // optional Metropolis uniforms: accept if |r|^2 >= u
@@ -107,8 +112,9 @@ template <typename T>
 void launch_gather(bool pairs, const DevLayout& L, const T* src, int m, const int* occ, T* A, int* err,
                    cudaStream_t st);
 template <typename T>
-void launch_step(bool pf, const DevLayout& L, const DevState<T>& S, const DevOperand& U, const DevOperand& V,
-                 const T* C, T* ratio_out, int* st_out, const StepCtl& ctl, int grid, cudaStream_t st);
+void launch_step(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& U,
+                 const DevOperand& V, const T* C, T* ratio_out, int* st_out, const StepCtl& ctl, int grid,
+                 cudaStream_t st);
 template <typename T>
 void launch_zero_split_tail(const DevLayout& L, const DevState<T>& S, const uint8_t* force, cudaStream_t st);
 // ---- refresh with the trailing updates on the tensor cores (refresh_oz.cu) ----

@@ -193,7 +193,7 @@ __device__ void propose_walker(const int w, const DevLayout L, const DevState<T>
                     s_cinv[i * MAXKK + j] = make_real<T>(v);
                 }
         } else {
-            const T* Cw = C + (long long)w * k2 * k2;
+            const T* Cw = C + (long long)w * L.kk * L.kk;   // slot of (2 kmax)^2 per walker
             for (int i = 0; i < k2; ++i)
                 for (int j = 0; j < k2; ++j) s_cinv[i * MAXKK + j] = Cw[i * k2 + j];
             T dC;
@@ -1138,110 +1138,6 @@ __global__ void __launch_bounds__(256) k_flush_df(DevLayout L, DevState<double> 
 
 #endif
 
-// ---------------------------------------------------------------------------
-// Persistent fused step for walkers of uneven n and k: one launch of a fixed
-// grid that pulls work from a device queue,
-//   items [0, W)          : propose walker order[i] (largest n^2 k first), then
-//                           the accept decision (mask, or Metropolis |r|^2 >= u)
-//   items [W, W + nacc)   : accept items (walker, chunk range), largest first,
-// An accept item waits (bounded, acquire) for its walker's propose flag; all
-// proposes are dequeued before any accept item, so every producer is already
-// running.  The last accept item of a walker commits log|value| and the sign.
-// Counters and flags are cleared by a memset in the same stream before the
-// launch, so the pair can be captured in a CUDA graph and replayed.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void st_release_gpu(int* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-// Spins (acquire loads, 64 ns naps) until *flag == want or `iters` polls have
-// failed; on giving up it records DEV_ERR_TIMEOUT in the sticky device error
-// and returns false, so the caller skips the dependent work and returns.
-__device__ __forceinline__ bool bounded_acquire_wait(const int* flag, int want, long long iters, int* err) {
-    for (long long i = 0; i < iters; ++i) {
-        if (ld_acquire_gpu(flag) == want) return true;
-        __nanosleep(64);
-    }
-    set_dev_error(err, DEV_ERR_TIMEOUT);
-    return false;
-}
-constexpr long long STEP_WAIT_POLLS = 1ll << 24;   // >= 1 s of polling
-
-template <typename T, bool PF, int NPL, int KKS>
-__global__ void __launch_bounds__(PT) k_step(DevLayout L, DevState<T> S, DevOperand U, DevOperand V, const T* C,
-                                              T* ratio_out, int* st_out, StepCtl ctl) {
-    __shared__ int s_item, s_ok;
-    const int total = L.W + (ctl.do_accept ? ctl.nacc : 0);
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(ctl.counter, 1);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
-        if (item >= total) break;
-        if (item < L.W) {
-            const int w = ctl.order[item];
-            propose_walker<T, PF, false>(w, L, S, U, V, C, ratio_out, st_out);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                bool acc = ctl.do_accept && S.pst[w] == 0;
-                if (acc && ctl.mask) acc = ctl.mask[w] != 0;
-                if (acc && ctl.u) acc = (double)s_abs2(S.ratio[w]) >= ctl.u[w];
-                ctl.acc[w] = acc ? 1 : 0;
-                __threadfence();
-                st_release_gpu(&ctl.prop_done[w], 1);
-            }
-        } else {
-            const int4 it = ctl.acc_items[item - L.W];
-            const int w = it.x;
-            if (threadIdx.x == 0) s_ok = bounded_acquire_wait(&ctl.prop_done[w], 1, STEP_WAIT_POLLS, S.err) ? 1 : 0;
-            __syncthreads();
-            if (s_ok && ctl.acc[w]) accept_item<T, false, NPL, KKS>(it, L, S, V, nullptr);
-            __syncthreads();
-            if (threadIdx.x == 0 && s_ok) {
-                __threadfence();
-                const int done = atomicAdd(&ctl.items_done[w], 1) + 1;
-                if (done == ctl.nacc_w[w] && ctl.acc[w]) {
-                    const T r = S.ratio[w];
-                    S.logabs[w] += log(s_absd(r));
-                    S.sgn[w] = s_renorm(S.sgn[w] * s_unit(r));
-                    S.pst[w] = 4;
-                }
-            }
-        }
-    }
-}
-
-template <typename T>
-void launch_step(bool pf, const DevLayout& L, const DevState<T>& S, const DevOperand& U, const DevOperand& V,
-                 const T* C, T* ratio_out, int* st_out, const StepCtl& ctl, int grid, cudaStream_t st) {
-    const int nmax = L.n_max;
-    int npl = 1;
-    while (32 * npl < nmax) npl *= 2;
-    size_t dyn = (size_t)2 * L.kk * nmax * sizeof(T);
-    if (dyn > 160 * 1024) dyn = 0;
-    const bool rank1 = L.kk == 1 && L.kvec == nullptr;
-#define LRU_STEP(N)                                                                                         \
-    case N:                                                                                                 \
-        if (pf) {                                                                                           \
-            auto k = rank1 ? k_step<T, true, N, 1> : k_step<T, true, N, 0>;                                  \
-            static bool attr = false;                                                                       \
-            if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); attr = true; } \
-            k<<<grid, PT, dyn, st>>>(L, S, U, V, C, ratio_out, st_out, ctl);                                \
-        } else {                                                                                            \
-            auto k = rank1 ? k_step<T, false, N, 1> : k_step<T, false, N, 0>;                                \
-            static bool attr = false;                                                                       \
-            if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); attr = true; } \
-            k<<<grid, PT, dyn, st>>>(L, S, U, V, C, ratio_out, st_out, ctl);                                \
-        }                                                                                                   \
-        break;
-    switch (npl) { LRU_STEP(1) LRU_STEP(2) LRU_STEP(4) LRU_STEP(8) LRU_STEP(16) LRU_STEP(32) LRU_STEP(64) default: break; }
-#undef LRU_STEP
-}
-
 // After the accept pass: log|value| += log|r|, sign *= r/|r|, tau += 1 (delayed)
 template <typename T>
 __global__ void k_commit(DevLayout L, DevState<T> S, const uint8_t* mask, bool delayed) {
@@ -1262,9 +1158,11 @@ __global__ void k_commit(DevLayout L, DevState<T> S, const uint8_t* mask, bool d
 // tiles with J <= L are computed and the mirror is written as the exact
 // negative transpose, so A_0^{-1} stays exactly skew.
 // ---------------------------------------------------------------------------
-template <typename T, bool PF>
+template <typename T, bool PF, int CH = 64>
 __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int w, int tau, int tJ, int tL,
-                                  T (*sP)[65], T (*sQ)[65], T (*sT)[33]) {
+                                  T* sP, T* sQ, T* sT) {
+    // sP, sQ: 32 x (CH + 1) slot chunks; sT: 32 x 33 result tile
+    constexpr int LD = CH + 1;
     const int n = L.nw(w), kk = L.kv(w);
     const int cu = tau * kk, Kc = L.Kc;
     const long long vo = L.vo(w);
@@ -1274,19 +1172,19 @@ __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int 
     T acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] = s_zero(T());
-    for (int c0 = 0; c0 < cu; c0 += 64) {
-        for (int e = threadIdx.x; e < 32 * 64; e += 256) {
-            const int r = e / 64, c = e % 64;
+    for (int c0 = 0; c0 < cu; c0 += CH) {
+        for (int e = threadIdx.x; e < 32 * CH; e += 256) {
+            const int r = e / CH, c = e % CH;
             const bool okc = c0 + c < cu;
-            sP[r][c] = (okc && j0 + r < n) ? S.P[(vo + j0 + r) * Kc + c0 + c] : s_zero(T());
-            sQ[r][c] = (okc && l0 + r < n) ? S.Q[(vo + l0 + r) * Kc + c0 + c] : s_zero(T());
+            sP[r * LD + c] = (okc && j0 + r < n) ? S.P[(vo + j0 + r) * Kc + c0 + c] : s_zero(T());
+            sQ[r * LD + c] = (okc && l0 + r < n) ? S.Q[(vo + l0 + r) * Kc + c0 + c] : s_zero(T());
         }
         __syncthreads();
-        const int cm = min(64, cu - c0);
+        const int cm = min(CH, cu - c0);
         for (int c = 0; c < cm; ++c) {
-            T pj = sP[tx][c];
+            T pj = sP[tx * LD + c];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = s_fma(pj, sQ[ty + 8 * q][c], acc[q]);
+            for (int q = 0; q < 4; ++q) acc[q] = s_fma(pj, sQ[(ty + 8 * q) * LD + c], acc[q]);
         }
         __syncthreads();
     }
@@ -1299,14 +1197,14 @@ __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int 
             T g = Gw[(long long)l * n + j];
             nv = PF ? (g + acc[q]) : (g - acc[q]);
         }
-        sT[ty + 8 * q][tx] = nv;
+        sT[(ty + 8 * q) * 33 + tx] = nv;
     }
     __syncthreads();
     if (!PF) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int j = j0 + tx, l = l0 + ty + 8 * q;
-            if (j < n && l < n) Gw[(long long)l * n + j] = sT[ty + 8 * q][tx];
+            if (j < n && l < n) Gw[(long long)l * n + j] = sT[(ty + 8 * q) * 33 + tx];
         }
     } else {
         // upper entries (j < l) are kept, lower ones written as their negatives
@@ -1315,9 +1213,9 @@ __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int 
             const int j = j0 + tx, l = l0 + ty + 8 * q;
             if (j < n && l < n) {
                 T v;
-                if (j < l) v = sT[ty + 8 * q][tx];
+                if (j < l) v = sT[(ty + 8 * q) * 33 + tx];
                 else if (j == l) v = s_zero(T());
-                else v = s_neg(sT[tx][ty + 8 * q]);  // same tile (diagonal tiles only)
+                else v = s_neg(sT[tx * 33 + ty + 8 * q]);  // same tile (diagonal tiles only)
                 Gw[(long long)l * n + j] = v;
             }
         }
@@ -1326,7 +1224,7 @@ __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int 
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int l = l0 + tx, j = j0 + ty + 8 * q;
-                if (j < n && l < n) Gw[(long long)j * n + l] = s_neg(sT[tx][ty + 8 * q]);
+                if (j < n && l < n) Gw[(long long)j * n + l] = s_neg(sT[tx * 33 + ty + 8 * q]);
             }
         }
     }
@@ -1351,11 +1249,216 @@ __global__ void __launch_bounds__(256) k_flush_native(DevLayout L, DevState<T> S
             for (int t = ti.first(ntl); t < ntl; t += gridDim.x) {
                 int tJ, tL;
                 TileIter::coords(t, nt, PF, tJ, tL);
-                flush_native_tile<T, PF>(L, S, w, tau, tJ, tL, sP, sQ, sT);
+                flush_native_tile<T, PF>(L, S, w, tau, tJ, tL, &sP[0][0], &sQ[0][0], &sT[0][0]);
             }
         }
     }
 }
+
+// Bounded waits of the persistent step (and of its self-test).
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// Spins (acquire loads, 64 ns naps) until *flag == want or `iters` polls have
+// failed; on giving up it records DEV_ERR_TIMEOUT in the sticky device error
+// and returns false, so the caller skips the dependent work and returns.
+__device__ __forceinline__ bool bounded_acquire_wait(const int* flag, int want, long long iters, int* err) {
+    for (long long i = 0; i < iters; ++i) {
+        if (ld_acquire_gpu(flag) == want) return true;
+        __nanosleep(64);
+    }
+    set_dev_error(err, DEV_ERR_TIMEOUT);
+    return false;
+}
+constexpr long long STEP_WAIT_POLLS = 1ll << 24;   // >= 1 s of polling
+
+#if !defined(LRU_NO_STEP)
+// ---------------------------------------------------------------------------
+// Persistent fused step for walkers of uneven n and k: one launch of a fixed
+// grid that pulls work from a device queue,
+//   items [0, W)                  : propose walker order[i] (largest n^2 k
+//                                   first), then the accept decision (mask,
+//                                   or Metropolis |r|^2 >= u)
+//   items [W, W + nacc)           : accept items (walker, chunk range),
+//                                   largest first; the last one of a walker
+//                                   commits log|value|, the sign (and, in the
+//                                   delayed form, tau += 1)
+//   items [W + nacc, + nflush)    : delayed form only: flush strips (walker,
+//                                   32 columns of A_0^{-1}); a strip waits for
+//                                   its walker's commit and, if tau reached K,
+//                                   folds the slots in (Eq. delayed_Ainv /
+//                                   pf_delayed_Ainv, FP64 tiles); the last
+//                                   strip of a walker resets tau.
+// Every wait (bounded, acquire) is on an item dequeued earlier, so its
+// producer is already running.  The delayed Pfaffian propose writes both
+// slots itself, so it has no accept items and commits in the propose item.
+// Counters and flags are cleared by a memset in the same stream before the
+// launch, so the pair can be captured in a CUDA graph and replayed.
+// ---------------------------------------------------------------------------
+
+// log|value| += log|r|, sign *= r / |r|, tau += 1 (delayed); proposal consumed
+template <typename T>
+__device__ __forceinline__ void commit_walker(const DevState<T>& S, int w, bool delayed) {
+    const T r = S.ratio[w];
+    S.logabs[w] += log(s_absd(r));
+    S.sgn[w] = s_renorm(S.sgn[w] * s_unit(r));
+    if (delayed) S.tau[w] += 1;
+    S.pst[w] = 4;
+}
+
+// Q^T u_a of the dense columns a of U (the (b_t^T U) / (B^T a_t) factors of
+// the delayed propose) for walker w, by the whole CTA (k_qtu_dense in one block)
+template <typename T>
+__device__ void qtu_block(int w, const DevLayout& L, const DevState<T>& S, const DevOperand& U) {
+    __shared__ T s_red[8 * 16];
+    __shared__ T s_out[16];
+    const int n = L.nw(w), kk = L.kv(w);
+    const int Kc = L.Kc, cu = S.tau[w] * kk;
+    const long long vo = L.vo(w);
+    for (int a = 0; a < kk; ++a) {
+        if ((U.mask >> a) & 1u) continue;
+        const T* u = vec_ptr<T>(U, L, w, a, n);
+        for (int c0 = 0; c0 < cu; c0 += 16) {
+            T part[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) part[q] = s_zero(T());
+            for (int j = threadIdx.x; j < n; j += PT) {
+                const T* qrow = S.Q + (vo + j) * Kc + c0;
+                const T uj = u[j];
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (c0 + q < cu) part[q] = s_fma(qrow[q], uj, part[q]);
+            }
+            block_reduce_vec<T, 16>(part, s_red, s_out);
+            if (threadIdx.x < 16 && c0 + threadIdx.x < cu)
+                S.QtU[((long long)w * Kc + c0 + threadIdx.x) * MAXKK + a] = s_out[threadIdx.x];
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+}
+
+constexpr int STEP_FLUSH_CH = 16;   // slot columns per chunk of a flush tile inside the step
+template <typename T>
+constexpr size_t step_flush_smem() {
+    return (size_t)(2 * 32 * (STEP_FLUSH_CH + 1) + 32 * 33) * sizeof(T);
+}
+
+template <typename T, bool PF, bool DEL, int NPL, int KKS>
+__global__ void __launch_bounds__(PT) k_step(DevLayout L, DevState<T> S, DevOperand U, DevOperand V, const T* C,
+                                              T* ratio_out, int* st_out, StepCtl ctl) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    __shared__ int s_item, s_ok, s_tau;
+    const int nacc = (ctl.do_accept && !(PF && DEL)) ? ctl.nacc : 0;
+    const int nfl = (ctl.do_accept && DEL) ? ctl.nflush : 0;
+    const int total = L.W + nacc + nfl;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(ctl.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        if (item < L.W) {
+            const int w = ctl.order[item];
+            if constexpr (DEL) qtu_block<T>(w, L, S, U);
+            propose_walker<T, PF, DEL>(w, L, S, U, V, C, ratio_out, st_out);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                bool acc = ctl.do_accept && S.pst[w] == 0;
+                if (acc && ctl.mask) acc = ctl.mask[w] != 0;
+                if (acc && ctl.u) acc = (double)s_abs2(S.ratio[w]) >= ctl.u[w];
+                ctl.acc[w] = acc ? 1 : 0;
+                if (PF && DEL) {
+                    // the slots are already written: commit here
+                    if (acc) commit_walker(S, w, true);
+                    __threadfence();
+                    st_release_gpu(&ctl.fin[w], 1);
+                }
+                __threadfence();
+                st_release_gpu(&ctl.prop_done[w], 1);
+            }
+        } else if (item < L.W + nacc) {
+            const int4 it = ctl.acc_items[item - L.W];
+            const int w = it.x;
+            if (threadIdx.x == 0) s_ok = bounded_acquire_wait(&ctl.prop_done[w], 1, STEP_WAIT_POLLS, S.err) ? 1 : 0;
+            __syncthreads();
+            if (s_ok && ctl.acc[w]) accept_item<T, DEL, NPL, KKS>(it, L, S, V, nullptr);
+            __syncthreads();
+            if (threadIdx.x == 0 && s_ok) {
+                __threadfence();
+                const int done = atomicAdd(&ctl.items_done[w], 1) + 1;
+                if (done == ctl.nacc_w[w]) {
+                    if (ctl.acc[w]) commit_walker(S, w, DEL);
+                    __threadfence();
+                    st_release_gpu(&ctl.fin[w], 1);
+                }
+            }
+        } else {
+            const int2 fi = ctl.flush_items[item - L.W - nacc];
+            const int w = fi.x, tL = fi.y;
+            if (threadIdx.x == 0) {
+                s_ok = bounded_acquire_wait(&ctl.fin[w], 1, STEP_WAIT_POLLS, S.err) ? 1 : 0;
+                s_tau = s_ok ? *(volatile const int*)&S.tau[w] : 0;
+            }
+            __syncthreads();
+            const int tau = s_tau;
+            if (s_ok && tau >= L.K) {
+                T* sP = reinterpret_cast<T*>(dyn_smem);
+                T* sQ = sP + 32 * (STEP_FLUSH_CH + 1);
+                T* sT = sQ + 32 * (STEP_FLUSH_CH + 1);
+                const int nt = (L.nw(w) + 31) / 32;
+                const int tJ_end = PF ? tL + 1 : nt;
+                for (int tJ = 0; tJ < tJ_end; ++tJ)
+                    flush_native_tile<T, PF, STEP_FLUSH_CH>(L, S, w, tau, tJ, tL, sP, sQ, sT);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && s_ok) {
+                __threadfence();
+                const int done = atomicAdd(&ctl.flush_done[w], 1) + 1;
+                if (done == ctl.nflush_w[w] && tau >= L.K) S.tau[w] = 0;
+            }
+        }
+    }
+}
+
+template <typename T>
+void launch_step(bool pf, bool delayed, const DevLayout& L, const DevState<T>& S, const DevOperand& U,
+                 const DevOperand& V, const T* C, T* ratio_out, int* st_out, const StepCtl& ctl, int grid,
+                 cudaStream_t st) {
+    const int nmax = L.n_max;
+    int npl = 1;
+    while (32 * npl < nmax) npl *= 2;
+    size_t dyn = (size_t)2 * L.kk * nmax * sizeof(T);
+    if (dyn > 160 * 1024) dyn = 0;   // accept items then carry use_smem = 0
+    if (delayed) {
+        dyn = std::max(dyn, (size_t)L.Kc * MAXKK * sizeof(T));   // Q^T U in the propose
+        dyn = std::max(dyn, step_flush_smem<T>());
+    }
+    const bool rank1 = L.kk == 1 && L.kvec == nullptr;
+#define LRU_STEP_K(PFV, DELV, N)                                                                          \
+    {                                                                                                     \
+        auto k = rank1 ? k_step<T, PFV, DELV, N, 1> : k_step<T, PFV, DELV, N, 0>;                         \
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);                 \
+        k<<<grid, PT, dyn, st>>>(L, S, U, V, C, ratio_out, st_out, ctl);                                  \
+    }
+#define LRU_STEP(N)                                                                                       \
+    case N:                                                                                               \
+        if (pf) {                                                                                         \
+            if (delayed) LRU_STEP_K(true, true, N) else LRU_STEP_K(true, false, N)                        \
+        } else {                                                                                          \
+            if (delayed) LRU_STEP_K(false, true, N) else LRU_STEP_K(false, false, N)                      \
+        }                                                                                                 \
+        break;
+    switch (npl) { LRU_STEP(1) LRU_STEP(2) LRU_STEP(4) LRU_STEP(8) LRU_STEP(16) LRU_STEP(32) LRU_STEP(64) default: break; }
+#undef LRU_STEP
+#undef LRU_STEP_K
+}
+#endif  // !LRU_NO_STEP
 
 template <typename T>
 __global__ void k_flush_finish(DevLayout L, DevState<T> S, const uint8_t* force) {
@@ -1719,8 +1822,6 @@ void launch_commit_moves(int W, int n, int k, int* occ, const int* slot, const i
     template void launch_flush_finish<T>(const DevLayout&, const DevState<T>&, const uint8_t*, cudaStream_t); \
     template void launch_set_delay_zero<T>(const DevLayout&, const DevState<T>&, cudaStream_t);             \
     template void launch_zero_split_tail<T>(const DevLayout&, const DevState<T>&, const uint8_t*, cudaStream_t); \
-    template void launch_step<T>(bool, const DevLayout&, const DevState<T>&, const DevOperand&, const DevOperand&, \
-                                 const T*, T*, int*, const StepCtl&, int, cudaStream_t);                      \
     template void launch_get_inverse<T>(bool, bool, const DevLayout&, const DevState<T>&, T*, cudaStream_t); \
     template void launch_form_row_moves<T>(const DevLayout&, const T*, int, const int*, const int*,         \
                                            const int*, T*, int*, cudaStream_t);                             \
@@ -1728,14 +1829,29 @@ void launch_commit_moves(int W, int n, int k, int* occ, const int* slot, const i
                                           const int*, T*, int*, cudaStream_t);                              \
     template void launch_gather<T>(bool, const DevLayout&, const T*, int, const int*, T*, int*, cudaStream_t);
 
-// The build compiles this file once per dtype (LRU_INST_DTYPE) in parallel.
+#define LRU_INST_STEP(T)                                                                                   \
+    template void launch_step<T>(bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&,        \
+                                 const DevOperand&, const T*, T*, int*, const StepCtl&, int, cudaStream_t);
+
+// The build compiles this file in parallel: once per dtype (LRU_INST_DTYPE)
+// without the persistent step (LRU_NO_STEP), and once per dtype with the step
+// alone (LRU_STEP_ONLY).
 #if defined(LRU_INST_DTYPE)
+#if !defined(LRU_STEP_ONLY)
 LRU_INST(LRU_INST_DTYPE)
+#endif
+#if !defined(LRU_NO_STEP)
+LRU_INST_STEP(LRU_INST_DTYPE)
+#endif
 #else
 LRU_INST(double)
 LRU_INST(float)
 LRU_INST(c128)
 LRU_INST(c64)
+LRU_INST_STEP(double)
+LRU_INST_STEP(float)
+LRU_INST_STEP(c128)
+LRU_INST_STEP(c64)
 #endif
 
 #if !defined(LRU_INST_DTYPE) || defined(LRU_INST_PRIMARY)

@@ -60,7 +60,10 @@ struct lru_ctx {
     int* d_order = nullptr;
     int* d_sitems = nullptr;
     int* d_nacc_w = nullptr;
-    int* d_ctl = nullptr;        // counter, prop_done[W], items_done[W]
+    int* d_ctl = nullptr;        // counter, prop_done[W], items_done[W], fin[W], flush_done[W]
+    int* d_fitems = nullptr;     // delayed: flush strips (walker, 32-column block)
+    int* d_nflush_w = nullptr;
+    int nflush = 0;
     uint8_t* d_acc = nullptr;
     int* d_never = nullptr;      // a flag no kernel writes (bounded-wait self-test)
     bool items_smem = true;
@@ -316,6 +319,18 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
             for (int c = 0; c < 4; ++c) per[items[q]].push_back(items[q + c]);
         for (int w : order) sitems.insert(sitems.end(), per[w].begin(), per[w].end());
     }
+    // delayed form: flush strips of 32 columns of A_0^{-1}, largest walkers first
+    std::vector<int> fitems, nflush_w(h->W, 0);
+    if (delayed)
+        for (int w : order) {
+            const int nt = (h->n_h[w] + 31) / 32;
+            for (int t = nt - 1; t >= 0; --t) {
+                fitems.push_back(w);
+                fitems.push_back(t);
+            }
+            nflush_w[w] = nt;
+        }
+    h->nflush = (int)fitems.size() / 2;
 
     // one allocation: persistent state first, then scratch and metadata
     const bool tc = delayed && cfg->flush != LRU_FLUSH_NATIVE && cfg->flush != LRU_FLUSH_DF &&
@@ -345,7 +360,9 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     const size_t oOrder = take((size_t)h->W * sizeof(int));
     const size_t oSItems = take(sitems.size() * sizeof(int));
     const size_t oNacc = take((size_t)h->W * sizeof(int));
-    const size_t oCtl = take((size_t)(1 + 2 * h->W) * sizeof(int));
+    const size_t oCtl = take((size_t)(1 + 4 * h->W) * sizeof(int));
+    const size_t oFit = take(std::max<size_t>(fitems.size(), 2) * sizeof(int));
+    const size_t oNfl = take((size_t)h->W * sizeof(int));
     const size_t oAcc = take((size_t)h->W);
     const size_t oNever = take(sizeof(int));
     h->bytes = off;
@@ -382,6 +399,8 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     h->d_sitems = (int*)(b + oSItems);
     h->d_nacc_w = (int*)(b + oNacc);
     h->d_ctl = (int*)(b + oCtl);
+    h->d_fitems = (int*)(b + oFit);
+    h->d_nflush_w = (int*)(b + oNfl);
     h->d_acc = (uint8_t*)(b + oAcc);
     h->d_never = (int*)(b + oNever);
     lru_status s = LRU_OK;
@@ -393,7 +412,10 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
         cudaMemcpy(h->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_order, order.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_sitems, sitems.data(), sitems.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(h->d_nacc_w, nacc_w.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(h->d_nacc_w, nacc_w.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!fitems.empty() &&
+         cudaMemcpy(h->d_fitems, fitems.data(), fitems.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaMemcpy(h->d_nflush_w, nflush_w.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
         s = LRU_ERR_CUDA;
     if (s != LRU_OK) {
         cudaGetLastError();
@@ -597,7 +619,6 @@ lru_status lru_step_persistent(lru_handle h, const lru_operand* U, const lru_ope
                                int32_t accept, const uint8_t* mask, const double* u, void* ratio, int32_t* st,
                                uint8_t* acc_out) {
     if (!h || !ratio) return LRU_ERR_ARG;
-    if (h->delayed) return LRU_ERR_UNSUPPORTED;
     if (!operand_ok(U, h->kk)) return LRU_ERR_ARG;
     if (!h->pf && !operand_ok(V, h->kk)) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
@@ -607,20 +628,26 @@ lru_status lru_step_persistent(lru_handle h, const lru_operand* U, const lru_ope
     ctl.counter = h->d_ctl;
     ctl.prop_done = h->d_ctl + 1;
     ctl.items_done = h->d_ctl + 1 + h->W;
+    ctl.fin = h->d_ctl + 1 + 2 * h->W;
+    ctl.flush_done = h->d_ctl + 1 + 3 * h->W;
     ctl.acc = acc_out ? acc_out : h->d_acc;
     ctl.order = h->d_order;
     ctl.acc_items = reinterpret_cast<const int4*>(h->d_sitems);
     ctl.nacc_w = h->d_nacc_w;
     ctl.nacc = h->nitems;
+    ctl.flush_items = reinterpret_cast<const int2*>(h->d_fitems);
+    ctl.nflush_w = h->d_nflush_w;
+    ctl.nflush = h->nflush;
     ctl.do_accept = accept != 0;
     ctl.mask = mask;
     ctl.u = u;
-    CK(cudaMemsetAsync(h->d_ctl, 0, (size_t)(1 + 2 * h->W) * sizeof(int), h->stream));
+    CK(cudaMemsetAsync(h->d_ctl, 0, (size_t)(1 + 4 * h->W) * sizeof(int), h->stream));
     DevLayout L = h->layout();
     h->launches += 1;
     prof_begin(h, LRU_PROF_PROPOSE);
     LRU_DISPATCH(h, {
-        launch_step<T>(h->pf, L, h->state<T>(), dU, dV, (const T*)C, (T*)ratio, st, ctl, 2 * h->n_sm, h->stream);
+        launch_step<T>(h->pf, h->delayed, L, h->state<T>(), dU, dV, (const T*)C, (T*)ratio, st, ctl, 2 * h->n_sm,
+                       h->stream);
     });
     prof_end(h, LRU_PROF_PROPOSE);
     lru_status s = cuda_check();

@@ -27,3 +27,13 @@ def test_candidates_respect_slot_capacity():
     assert c == sorted(c) and all(2 <= x <= 64 for x in c)
     c2 = A.candidates("pf", 256, 2)          # 2k = 4 columns per step: K <= 16
     assert all(4 * x <= 64 for x in c2) and 4 in c2
+
+
+def test_flush_candidates_keep_fp64_class_kernels():
+    torch = pytest.importorskip("torch")
+    A = at()
+    L = A.L
+    # FP64 tiles always; split product where n % 128 == 0; double-float for F64
+    assert A.flush_candidates("det", 256, 1, torch.float64) == [L.FLUSH_NATIVE, L.FLUSH_SPLIT, L.FLUSH_DF]
+    assert A.flush_candidates("det", 200, 1, torch.float64) == [L.FLUSH_NATIVE, L.FLUSH_DF]
+    assert A.flush_candidates("pf", 256, 1, torch.complex128) == [L.FLUSH_NATIVE]

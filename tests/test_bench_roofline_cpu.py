@@ -33,11 +33,14 @@ def test_det_accept_plain_and_delayed():
     dl = bench.accept_roofline(16, "native", n, W, 1.9, HBM)
     assert dl["bytes_per_launch"] == n * n * 8 * W                 # one pass over A_0^{-1}
     assert dl["fp64_flop_per_launch"] == 2 * n * n * W
-    assert dl["bound"] == "alu"
-    # the headline accept's DRAM traffic is scaled from the 64-walker capture
-    assert math.isclose(dl["traffic"], bench.ACCEPT_DELAYED_TRAFFIC_PER_WALKER_N1024 * W)
-    df = bench.accept_roofline(16, "df", n, W, 1.9, HBM)
+    assert dl["bound"] == "alu" and dl["traffic"] is None
+    df = bench.accept_roofline(16, "df", n, W, 1.5, HBM)
     assert df["bound"] == "hbm" and df["fp64_flop_per_launch"] == 0
+    # the headline accept's DRAM traffic is scaled from the 64-walker capture
+    assert math.isclose(df["traffic"], bench.ACCEPT_DF_TRAFFIC_PER_WALKER_N1024 * W)
+    # complex128: 16-byte scalars, four real FMAs per complex one
+    c = bench.accept_roofline(16, "native", 512, 4096, 1.0, HBM, s=16, cf=4)
+    assert c["bytes_per_launch"] == 512 * 512 * 16 * 4096 and c["fp64_flop_per_launch"] == 4 * 2 * 512 * 512 * 4096
 
 
 def test_pf_accept_propose_and_flush():

@@ -170,9 +170,116 @@ def test_autotuner_returns_a_measured_setting(tmp_path, monkeypatch):
     import paper_2602_05255_gb300.autotune as AT
     AT = importlib.reload(AT)
     res = AT.tune("det", 256, 1, walkers=64, steps=24, delays=[4, 8], tiles=[32, 64])
-    assert res["delay"] in (0, 4, 8) and res["tile_chunks"] in (32, 64)
-    assert len(res["trials"]) == 6 and all(t["updates_per_s"] > 0 for t in res["trials"])
+    L = AT.L
+    assert res["delay"] in (0, 4, 8) and res["tile_chunks"] in (0, 32, 64)
+    assert res["flush"] in (L.FLUSH_NATIVE, L.FLUSH_SPLIT, L.FLUSH_DF) and res["arith"] in (0, 1)
+    # 2 GEMV arithmetics x (plain + 2 delays x 3 flush kernels), then 2 accept tiles
+    assert len(res["trials"]) == 2 * (1 + 2 * 3) + 2 and all(t["updates_per_s"] > 0 for t in res["trials"])
+    st = AT.make_state("det", 8, 256, tuned=res)      # the handle takes the tuned setting
+    assert st.delay == res["delay"]
+    st.close()
     assert res["heuristic_delay"] == AT.heuristic_delay("det", 256, 1) == 26
     assert (tmp_path / "tune.json").exists()
     again = AT.tune("det", 256, 1, walkers=64, steps=24, delays=[4, 8], tiles=[32, 64])
     assert again == res   # served from the cache
+
+
+@pytest.mark.parametrize("dt", ["c128", "f64"])
+@pytest.mark.parametrize("kind", ["det", "pf"])
+def test_ragged_delayed_persistent_chain_graph(dt, kind):
+    """The delayed form inside the persistent launch (Sec. 2.3 / 3.3): walkers
+    of uneven n and k, a Metropolis-like mask so that every walker has its own
+    delay counter, the slots of walkers that reach K folded into A_0^{-1} in
+    the same launch; one step captured in a CUDA graph and replayed with new
+    operands.  Every walker against the oracle's delayed chain, replaying the
+    GPU's acceptance decisions."""
+    L = lrugb()
+    tdt = torch.complex128 if dt == "c128" else torch.float64
+    cplx = dt == "c128"
+    npdt = np.complex128 if cplx else np.float64
+    W, K, steps = 12, 3, 11
+    g = np.random.Generator(np.random.PCG64(1300 + (kind == "pf")))
+    n_w = g.choice([16, 32, 48, 96] if kind == "det" else [16, 32, 48, 96], W)
+    k_w = g.choice([1, 2, 3] if kind == "det" else [1, 2], W)
+    kmax = int(k_w.max())
+    slots = kmax if kind == "det" else 2 * kmax
+    rnd = lambda *sh: (g.standard_normal(sh) + (1j * g.standard_normal(sh) if cplx else 0))
+    if kind == "det":
+        A = [rnd(n, n) / np.sqrt(n) + 2.5 * np.eye(n) for n in n_w]
+    else:
+        A = []
+        for n in n_w:
+            M = rnd(n, n) / np.sqrt(n)
+            A.append(M - M.T + 2.5 * np.kron(np.eye(n // 2), np.array([[0, 1], [-1, 0]])))
+    st = L.LowRankState(kind, W, [int(x) for x in n_w], k=kmax, dtype=tdt, delay=K,
+                        k_per_walker=[int(x) for x in k_w])
+    st.init(tdev(flat_mats(A), tdt))
+    kk_w = k_w if kind == "det" else 2 * k_w
+    Ud = torch.zeros(int(np.sum(n_w)) * slots, dtype=tdt, device="cuda")
+    Vd = torch.zeros_like(Ud)
+    Cd = torch.zeros(W * slots * slots, dtype=tdt, device="cuda")   # pf: C per walker (2k x 2k, skew)
+    mask = torch.zeros(W, dtype=torch.uint8, device="cuda")
+    ratio = torch.empty(W, dtype=tdt, device="cuda")
+    status = torch.empty(W, dtype=torch.int32, device="cuda")
+    acc = torch.empty(W, dtype=torch.uint8, device="cuda")
+
+    def ops_for_step():
+        U = [rnd(kk, n) * 0.3 / np.sqrt(n) for n, kk in zip(n_w, kk_w)]
+        V = [rnd(kk, n) * 0.3 / np.sqrt(n) for n, kk in zip(n_w, kk_w)]
+        Cs = []
+        for kk in kk_w:
+            Cm = rnd(kk, kk)
+            Cs.append(Cm - Cm.T)
+        return U, V, Cs
+
+    def fill(U, V, Cs, m):
+        Ud.copy_(tdev(flat_ops(U, n_w, slots, npdt), tdt))
+        Vd.copy_(tdev(flat_ops(V, n_w, slots, npdt), tdt))
+        Cflat = np.zeros(W * slots * slots, dtype=npdt)
+        for w, Cm in enumerate(Cs):
+            kk = Cm.shape[0]
+            # walker w's 2k_w x 2k_w C, row-major, at w (2 kmax)^2
+            Cflat[w * slots * slots: w * slots * slots + kk * kk] = Cm.reshape(-1)
+        Cd.copy_(tdev(Cflat, tdt))
+        mask.copy_(tdev(m.astype(np.uint8)))
+
+    def step():
+        Cp = Cd if kind == "pf" else None
+        st.step_persistent(L.Operand(dense=Ud), None if kind == "pf" else L.Operand(dense=Vd), Cmat=Cp,
+                           accept=True, mask=mask, ratio=ratio, status=status, acc=acc)
+
+    rec = []
+    graph = None
+    for s in range(steps):
+        U, V, Cs = ops_for_step()
+        m = g.random(W) < 0.7
+        fill(U, V, Cs, m)
+        if s == 0:
+            step()                              # one eager call before capturing
+        elif s == 1:
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                step()
+            graph.replay()
+        else:
+            graph.replay()
+        torch.cuda.synchronize()
+        rec.append((U, V, Cs, ratio.cpu().numpy().copy(), status.cpu().numpy().copy(), acc.cpu().numpy().copy()))
+    st.check_device_error()
+    tau = st.tau().cpu().numpy()
+    inv = unflat_mats(st.inverse().cpu().numpy(), n_w)
+    for w in range(W):
+        car = O.init_det_carrier(A[w], K) if kind == "det" else O.init_pf_carrier(A[w], K)
+        for s, (U, V, Cs, r, stt, ac) in enumerate(rec):
+            assert stt[w] == 0
+            if kind == "det":
+                ref = O.det_lru_delayed(car, U[w].T, V[w], accept=bool(ac[w]))
+            else:
+                ref = O.pf_lru_delayed(car, U[w].T, Cs[w], accept=bool(ac[w]))
+            assert rel(r[w], ref) <= 1e-9, (w, s, r[w], ref)
+        assert tau[w] == car.tau, (w, tau[w], car.tau)
+        assert fro_rel(inv[w], O.carrier_inverse(car)) <= 1e-9, w
+    # every walker was due at some step, and not all at the same ones
+    accepted = np.array([a for (_, _, _, _, _, a) in rec])
+    assert (accepted.sum(0) >= K).all() and len(set(accepted.sum(0) % K)) > 1
