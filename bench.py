@@ -105,10 +105,13 @@ PF_ARMS = {
 # the GB300 datasheet); a DFMA probe measured 1.06 TFLOP/s at 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_SRC = "derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"
+# FP32 pipe (single-precision dtypes): 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_SRC = "derived FP32 peak: 152 SMs x 128 FFMA/clk x 2 x 2.07 GHz"
 # DRAM bytes per walker of one launch of the double-float delayed accept
 # (k_accept_delayed_warp_df) at n = 1024, from an ncu capture at 64 walkers:
 # one pass over each walker's A_0^{-1}, so a full launch is this times W.
-ACCEPT_DF_TRAFFIC_PER_WALKER_N1024 = (548.729088e6 + 4.756992e6) / 64
+ACCEPT_DF_TRAFFIC_PER_WALKER_N1024 = (548.643328e6 + 4.782592e6) / 64
 
 
 def parse(argv=None):
@@ -337,20 +340,22 @@ def timed_steps(torch, st, step, args, dist, dev):
 # --------------------------------------------------------------------------
 # rooflines (algorithmic bytes and flops per launch; DESIGN tables)
 # --------------------------------------------------------------------------
-def bound_of(byt, fp64_flop, ms, hbm):
-    """Roofline of one launch: HBM bytes against the FP64 pipe, whichever
-    takes longer at its peak binds; achieved and frac are against that bound."""
+def bound_of(byt, fp64_flop, ms, hbm, fp32=False):
+    """Roofline of one launch: HBM bytes against the FP64 pipe (fp32: the
+    flops are single precision, against the FP32 pipe), whichever takes longer
+    at its peak binds; achieved and frac are against that bound."""
     if not ms:
         return None
-    t_hbm, t_fp64 = byt / (hbm * 1e9), fp64_flop / (FP64_PEAK_TFLOPS * 1e12)
+    peak, src = (FP32_PEAK_TFLOPS, FP32_SRC) if fp32 else (FP64_PEAK_TFLOPS, FP64_SRC)
+    t_hbm, t_fp64 = byt / (hbm * 1e9), fp64_flop / (peak * 1e12)
     out = {"bytes_per_launch": byt, "fp64_flop_per_launch": fp64_flop, "ms_per_launch": ms, "traffic": None,
            "hbm": {"achieved": byt / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"},
            "time_at_hbm_peak_ms": t_hbm * 1e3, "time_at_fp64_peak_ms": t_fp64 * 1e3}
     out["hbm"]["frac"] = out["hbm"]["achieved"] / hbm
     if fp64_flop and t_fp64 > t_hbm:
         ach = fp64_flop / (ms / 1e3) / 1e12
-        out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "peak_source": FP64_SRC})
+        out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "peak_source": src})
     else:
         out.update({"bound": "hbm", "achieved": out["hbm"]["achieved"], "peak": hbm, "unit": "GB/s",
                     "frac": out["hbm"]["frac"], "peak_source": "HBM of measured (MEASURED_PEAKS.json hbm_gbs)"})
@@ -1019,7 +1024,7 @@ def main_ragged(args, cfg, torch, L, rank, world, dist):
     byt = float(np.sum(2 * n2 * s_b + 2 * n2 * s_b / K))
     flop = float(np.sum(2 * 2 * n2 * k_w * cf + 2 * n2 * k_w * cf))
     hbm, _, _ = load_peaks()
-    roof = bound_of(byt, flop, ms / args.steps, hbm)
+    roof = bound_of(byt, flop, ms / args.steps, hbm, fp32=cfg["dtype"] == "c64")
     roof["kernel"] = "persistent step (propose + accept + flush, one launch)"
     # the adjoint: propose-only launch + lru_backward_det (d log r / d(U, V, A))
     U, V = sets[0]
