@@ -43,7 +43,7 @@ __all__ = [
     "onehot_matrix", "det_ratio_direct", "pf_ratio_direct",
     "det_lru", "DetCarrier", "init_det_carrier", "det_lru_delayed",
     "pf_lru", "PfCarrier", "init_pf_carrier", "pf_lru_delayed",
-    "carrier_inverse", "det_row_move", "pf_row_col_move",
+    "carrier_inverse", "det_row_move", "pf_row_col_move", "pf_two_particle_move",
     "slater_matrix", "pairing_matrix",
 ]
 
@@ -498,3 +498,28 @@ def pf_row_col_move(F, pos, i, new_site):
     B[:, 0] = x
     B[i, 1] = 1
     return B, -skew_eye(1, dtype=F.dtype)
+
+
+def pf_two_particle_move(F, pos, p, q, new_p, new_q):
+    """Two particles moved at once: rows and columns p and q replaced (Sec.
+    3.2, the update of 2 rows and 2 columns, A' - A = -u J u^T with
+    u = [x, y, e_p, e_q]).  Entry (p, q) of the change is x_q - y_p, so
+    x_j = F(r'_p, r'_j) - F(r_p, r_j) with the new sites of both particles
+    (x_p = 0), y_j = F(r'_q, r_j) - F(r_q, r_j) at the old sites, y_p = 0
+    (its diagonal entry y_q cancels).  Returns (B, C) with B = [x, y, e_p,
+    e_q] and C = -J (2 x 2 blocks)."""
+    F = np.asarray(F)
+    pos = np.asarray(pos)
+    new_pos = pos.copy()
+    new_pos[p] = new_p
+    new_pos[q] = new_q
+    x = F[new_p, new_pos] - F[pos[p], pos]
+    y = F[new_q, pos] - F[pos[q], pos]
+    y[p] = 0
+    n = len(pos)
+    B = np.zeros((n, 4), dtype=F.dtype)
+    B[:, 0] = x
+    B[:, 1] = y
+    B[p, 2] = 1
+    B[q, 3] = 1
+    return B, -skew_eye(2, dtype=F.dtype)

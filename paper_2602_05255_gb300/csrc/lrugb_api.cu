@@ -8,11 +8,24 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lrugb.h"
 #include "common.cuh"
 #include "internal.h"
 
 using namespace lru;
+
+namespace {
+// An NVTX range around each C-ABI call (named after the call), so that a
+// profiler's timeline groups the kernels of a call under it.  NVTX is
+// header-only and costs nothing when no profiler is attached.
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+};
+}  // namespace
+#define LRU_RANGE() NvtxScope lru_nvtx_scope_(__func__)
 
 namespace {
 
@@ -207,6 +220,7 @@ const char* lru_status_string(lru_status s) {
 const char* lru_version(void) { return "lrugb 0.1.0 sm_103a"; }
 
 lru_status lru_create(const lru_config* cfg, lru_handle* out) {
+    LRU_RANGE();
     if (!cfg || !out) return LRU_ERR_ARG;
     *out = nullptr;
     if (cfg->kind != LRU_DET && cfg->kind != LRU_PF) return LRU_ERR_ARG;
@@ -428,6 +442,7 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
 }
 
 lru_status lru_destroy(lru_handle h) {
+    LRU_RANGE();
     if (!h) return LRU_ERR_ARG;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -445,12 +460,14 @@ lru_status lru_destroy(lru_handle h) {
 }
 
 lru_status lru_set_stream(lru_handle h, void* stream) {
+    LRU_RANGE();
     if (!h) return LRU_ERR_ARG;
     h->stream = (cudaStream_t)stream;
     return LRU_OK;
 }
 
 lru_status lru_device_bytes(lru_handle h, size_t* bytes) {
+    LRU_RANGE();
     if (!h || !bytes) return LRU_ERR_ARG;
     *bytes = h->bytes + (h->ws ? (size_t)h->nws * h->n_max * h->n_max * dtype_size(h->dtype) : 0) + h->oz_bytes + h->ozM_bytes;
     return LRU_OK;
@@ -538,18 +555,21 @@ static lru_status do_init(lru_handle h, const void* A, const uint8_t* mask, doub
 }
 
 lru_status lru_init_det(lru_handle h, const void* A, double* logabs, void* sign) {
+    LRU_RANGE();
     if (!h) return LRU_ERR_ARG;
     if (h->pf) return LRU_ERR_STATE;
     return do_init(h, A, nullptr, nullptr, logabs, sign, false);
 }
 
 lru_status lru_init_pf(lru_handle h, const void* A, double* logabs, void* sign) {
+    LRU_RANGE();
     if (!h) return LRU_ERR_ARG;
     if (!h->pf) return LRU_ERR_STATE;
     return do_init(h, A, nullptr, nullptr, logabs, sign, false);
 }
 
 lru_status lru_refresh_from_scratch(lru_handle h, const void* A, const uint8_t* mask, double* drift) {
+    LRU_RANGE();
     if (!h) return LRU_ERR_ARG;
     return do_init(h, A, mask, drift, nullptr, nullptr, true);
 }
@@ -572,6 +592,7 @@ static bool operand_ok(const lru_operand* o, int kk) {
 }
 
 lru_status lru_propose_det(lru_handle h, const lru_operand* U, const lru_operand* V, void* ratio, int32_t* st) {
+    LRU_RANGE();
     if (!h || !ratio) return LRU_ERR_ARG;
     if (h->pf) return LRU_ERR_STATE;
     if (!operand_ok(U, h->kk) || !operand_ok(V, h->kk)) return LRU_ERR_ARG;
@@ -594,6 +615,7 @@ lru_status lru_propose_det(lru_handle h, const lru_operand* U, const lru_operand
 }
 
 lru_status lru_propose_pf(lru_handle h, const lru_operand* B, const void* C, void* ratio, int32_t* st) {
+    LRU_RANGE();
     if (!h || !ratio) return LRU_ERR_ARG;
     if (!h->pf) return LRU_ERR_STATE;
     if (!operand_ok(B, h->kk)) return LRU_ERR_ARG;
@@ -618,6 +640,7 @@ lru_status lru_propose_pf(lru_handle h, const lru_operand* B, const void* C, voi
 lru_status lru_step_persistent(lru_handle h, const lru_operand* U, const lru_operand* V, const void* C,
                                int32_t accept, const uint8_t* mask, const double* u, void* ratio, int32_t* st,
                                uint8_t* acc_out) {
+    LRU_RANGE();
     if (!h || !ratio) return LRU_ERR_ARG;
     if (!operand_ok(U, h->kk)) return LRU_ERR_ARG;
     if (!h->pf && !operand_ok(V, h->kk)) return LRU_ERR_ARG;
@@ -696,6 +719,7 @@ static lru_status do_flush(lru_handle h, const uint8_t* force) {
 }
 
 lru_status lru_accept(lru_handle h, const uint8_t* mask) {
+    LRU_RANGE();
     if (!h) return LRU_ERR_ARG;
     if (!h->has_prop) return LRU_ERR_STATE;
     CK(cudaSetDevice(h->device));
@@ -715,6 +739,7 @@ lru_status lru_accept(lru_handle h, const uint8_t* mask) {
 }
 
 lru_status lru_flush_delayed(lru_handle h, const uint8_t* mask) {
+    LRU_RANGE();
     if (!h) return LRU_ERR_ARG;
     if (!h->delayed) return LRU_OK;
     CK(cudaSetDevice(h->device));
@@ -731,6 +756,7 @@ lru_status lru_flush_delayed(lru_handle h, const uint8_t* mask) {
 }
 
 lru_status lru_get_inverse(lru_handle h, void* out) {
+    LRU_RANGE();
     if (!h || !out) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     DevLayout L = h->layout();
@@ -740,6 +766,7 @@ lru_status lru_get_inverse(lru_handle h, void* out) {
 }
 
 lru_status lru_get_logvalue(lru_handle h, double* logabs, void* sign) {
+    LRU_RANGE();
     if (!h) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     if (logabs) CK(cudaMemcpyAsync(logabs, h->logabs, h->W * sizeof(double), cudaMemcpyDefault, h->stream));
@@ -748,6 +775,7 @@ lru_status lru_get_logvalue(lru_handle h, double* logabs, void* sign) {
 }
 
 lru_status lru_get_delay(lru_handle h, int32_t* tau) {
+    LRU_RANGE();
     if (!h || !tau) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     CK(cudaMemcpyAsync(tau, h->tau, h->W * sizeof(int), cudaMemcpyDefault, h->stream));
@@ -755,12 +783,14 @@ lru_status lru_get_delay(lru_handle h, int32_t* tau) {
 }
 
 lru_status lru_state_bytes(lru_handle h, size_t* bytes) {
+    LRU_RANGE();
     if (!h || !bytes) return LRU_ERR_ARG;
     *bytes = h->persist_bytes;
     return LRU_OK;
 }
 
 lru_status lru_save_state(lru_handle h, void* buf) {
+    LRU_RANGE();
     if (!h || !buf) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     CK(cudaMemcpyAsync(buf, h->base, h->persist_bytes, cudaMemcpyDefault, h->stream));
@@ -768,6 +798,7 @@ lru_status lru_save_state(lru_handle h, void* buf) {
 }
 
 lru_status lru_load_state(lru_handle h, const void* buf) {
+    LRU_RANGE();
     if (!h || !buf) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     CK(cudaMemcpyAsync(h->base, buf, h->persist_bytes, cudaMemcpyDefault, h->stream));
@@ -776,6 +807,7 @@ lru_status lru_load_state(lru_handle h, const void* buf) {
 }
 
 lru_status lru_check_device_error(lru_handle h) {
+    LRU_RANGE();
     if (!h) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     CK(cudaStreamSynchronize(h->stream));
@@ -788,6 +820,7 @@ lru_status lru_check_device_error(lru_handle h) {
 }
 
 lru_status lru_wait_selftest(lru_handle h, int64_t polls) {
+    LRU_RANGE();
     if (!h || polls < 0 || polls > (1ll << 24)) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     CK(cudaMemsetAsync(h->d_never, 0, sizeof(int), h->stream));
@@ -798,6 +831,7 @@ lru_status lru_wait_selftest(lru_handle h, int64_t polls) {
 
 lru_status lru_form_row_moves(lru_handle h, const void* Phi, int32_t m, const int32_t* occ, const int32_t* slot,
                               const int32_t* new_row, void* V_out, int32_t* idx_out) {
+    LRU_RANGE();
     if (!h || !Phi || !occ || !slot || !new_row || !V_out || !idx_out || m < 1) return LRU_ERR_ARG;
     if (h->pf || h->n_uni <= 0) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
@@ -811,6 +845,7 @@ lru_status lru_form_row_moves(lru_handle h, const void* Phi, int32_t m, const in
 
 lru_status lru_form_pf_moves(lru_handle h, const void* F, int32_t m, const int32_t* pos, const int32_t* slot,
                              const int32_t* new_site, void* B_out, int32_t* idx_out) {
+    LRU_RANGE();
     if (!h || !F || !pos || !slot || !new_site || !B_out || !idx_out || m < 1) return LRU_ERR_ARG;
     if (!h->pf || h->n_uni <= 0 || h->kk != 2) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
@@ -824,6 +859,7 @@ lru_status lru_form_pf_moves(lru_handle h, const void* F, int32_t m, const int32
 
 lru_status lru_commit_moves(lru_handle h, int32_t* occ, const int32_t* slot, const int32_t* new_row,
                             const uint8_t* mask) {
+    LRU_RANGE();
     if (!h || !occ || !slot || !new_row) return LRU_ERR_ARG;
     if (h->n_uni <= 0) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
@@ -833,6 +869,7 @@ lru_status lru_commit_moves(lru_handle h, int32_t* occ, const int32_t* slot, con
 }
 
 lru_status lru_gather_rows(lru_handle h, const void* Phi, int32_t m, const int32_t* occ, void* A_out) {
+    LRU_RANGE();
     if (!h || !Phi || !occ || !A_out || m < 1) return LRU_ERR_ARG;
     if (h->n_uni <= 0) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
@@ -843,6 +880,7 @@ lru_status lru_gather_rows(lru_handle h, const void* Phi, int32_t m, const int32
 }
 
 lru_status lru_gather_pairs(lru_handle h, const void* F, int32_t m, const int32_t* pos, void* A_out) {
+    LRU_RANGE();
     if (!h || !F || !pos || !A_out || m < 1) return LRU_ERR_ARG;
     if (h->n_uni <= 0) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
@@ -853,6 +891,7 @@ lru_status lru_gather_pairs(lru_handle h, const void* F, int32_t m, const int32_
 }
 
 lru_status lru_log_ratio(lru_handle h, void* logr) {
+    LRU_RANGE();
     if (!h || !logr) return LRU_ERR_ARG;
     if (!h->has_prop) return LRU_ERR_STATE;
     CK(cudaSetDevice(h->device));
@@ -883,14 +922,17 @@ static lru_status do_backward(lru_handle h, bool pf, const void* g, void* gU, vo
 }
 
 lru_status lru_backward_det(lru_handle h, const void* g, void* gU, void* gV, void* gA) {
+    LRU_RANGE();
     return do_backward(h, false, g, gU, gV, gA, nullptr);
 }
 
 lru_status lru_backward_pf(lru_handle h, const void* g, void* gB, void* gC, void* gA) {
+    LRU_RANGE();
     return do_backward(h, true, g, gB, nullptr, gA, gC);
 }
 
 lru_status lru_backward_logvalue(lru_handle h, const void* g, void* gA) {
+    LRU_RANGE();
     if (!h || !g || !gA) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     DevLayout L = h->layout();
@@ -900,6 +942,7 @@ lru_status lru_backward_logvalue(lru_handle h, const void* g, void* gA) {
 }
 
 lru_status lru_scatter_rows_add(lru_handle h, const void* gA, const int32_t* rows, int32_t m, void* gPhi) {
+    LRU_RANGE();
     if (!h || !gA || !rows || !gPhi || m < 1) return LRU_ERR_ARG;
     if (h->n_uni <= 0) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
@@ -910,12 +953,14 @@ lru_status lru_scatter_rows_add(lru_handle h, const void* gA, const int32_t* row
 }
 
 lru_status lru_profile_enable(lru_handle h, int32_t on) {
+    LRU_RANGE();
     if (!h) return LRU_ERR_ARG;
     h->prof_on = on != 0;
     return LRU_OK;
 }
 
 lru_status lru_profile_read(lru_handle h, int32_t cls, double* total_ms, int64_t* launches) {
+    LRU_RANGE();
     if (!h || cls < 0 || cls >= LRU_PROF_CLASSES) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     CK(cudaStreamSynchronize(h->stream));
@@ -933,6 +978,7 @@ lru_status lru_profile_read(lru_handle h, int32_t cls, double* total_ms, int64_t
 }
 
 lru_status lru_launch_count(lru_handle h, int64_t* count) {
+    LRU_RANGE();
     if (!h || !count) return LRU_ERR_ARG;
     *count = h->launches;
     return LRU_OK;
@@ -967,11 +1013,13 @@ static lru_status batched_dense(bool pf, int32_t dtype, int64_t W, int32_t n, co
 
 lru_status lru_slogdet_batched(int32_t dtype, int64_t W, int32_t n, const void* A, double* logabs, void* sign,
                                void* stream) {
+    LRU_RANGE();
     return batched_dense(false, dtype, W, n, A, logabs, sign, stream);
 }
 
 lru_status lru_slogpf_batched(int32_t dtype, int64_t W, int32_t n, const void* A, double* logabs, void* sign,
                               void* stream) {
+    LRU_RANGE();
     if (n & 1) return LRU_ERR_ARG;
     return batched_dense(true, dtype, W, n, A, logabs, sign, stream);
 }

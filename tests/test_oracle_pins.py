@@ -218,6 +218,41 @@ def test_pf_row_col_move_is_position_change():
     assert np.allclose(A + B @ C @ B.T, A2, atol=1e-15)
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+def test_pf_two_particle_move_is_position_change(cplx):
+    # two particles moved at once: the 2-rows-2-columns form of Sec. 3.2,
+    # A' - A = -u J u^T with u = [x, y, e_p, e_q]; its (p, q) entry is x_q - y_p
+    g = rng(83 + cplx)
+    G = g.standard_normal((18, 18)) + (1j * g.standard_normal((18, 18)) if cplx else 0)
+    F = G - G.T
+    pos = np.array([1, 4, 5, 8, 10, 13, 16])
+    p, q, new_p, new_q = 1, 4, 17, 2
+    B, C = O.pf_two_particle_move(F, pos, p, q, new_p, new_q)
+    pos2 = pos.copy()
+    pos2[p], pos2[q] = new_p, new_q
+    A, A2 = O.pairing_matrix(F, pos), O.pairing_matrix(F, pos2)
+    assert np.allclose(A + B @ C @ B.T, A2, rtol=0, atol=1e-14)
+    assert np.array_equal(C, -O.skew_eye(2))
+    assert np.array_equal(B[:, 2], np.eye(len(pos))[p]) and np.array_equal(B[:, 3], np.eye(len(pos))[q])
+    assert (A2 - A)[p, q] == pytest.approx(B[q, 0] - B[p, 1], abs=1e-14)
+
+
+def test_pf_two_particle_ratio_brute_force():
+    # pf(A') / pf(A) by the pairing sum (App. A.1) against the low-rank ratio of
+    # the two-particle operands (App. A.2, k = 2)
+    g = rng(85)
+    G = g.standard_normal((14, 14))
+    F = G - G.T
+    pos = np.array([0, 2, 3, 6, 7, 9, 11, 12])
+    B, C = O.pf_two_particle_move(F, pos, 2, 5, 13, 1)
+    pos2 = pos.copy()
+    pos2[2], pos2[5] = 13, 1
+    A, A2 = O.pairing_matrix(F, pos), O.pairing_matrix(F, pos2)
+    exact = O.pf_pairings(A2) / O.pf_pairings(A)
+    r = O.pf_lru(O.skew_part(O.inv(A)), B, C)
+    assert r == pytest.approx(exact, rel=1e-11)
+
+
 # --------------------------------------------------------------------------
 # plain LRU
 # --------------------------------------------------------------------------
