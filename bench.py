@@ -73,7 +73,13 @@ PRESETS = {
            "main": "delayed_fp64gemv"},
     "c5": {"kind": "ragged", "walkers": 2048, "ns": (128, 256, 512, 1024), "ks": (1, 2, 4, 8), "delay": 4,
            "dtype": "c128", "refresh_every": 0},
+    # Sec. 4.1 Fig. 1 on GB300 (context): direct batched slogdet / slogpf of the
+    # updated matrices against the LRU ratio, without and with the inverse update
+    "fig1": {"kind": "fig1", "walkers": 1024, "ns": (16, 32, 64, 128, 256, 512, 1024), "dtype": "f64",
+             "refresh_every": 0, "delay": 0},
 }
+FIG1_METRIC = ("speedup at n=1024 of the LRU ratio with the inverse update over the batched direct determinant, "
+               "1024 walkers, k=1 (Sec. 4.1 Fig. 1 on GB300)")
 # complex dtypes: the arms that apply (FP64-class arithmetic on complex scalars)
 COMPLEX_ARMS = {"det": ("plain,delayed_native", "delayed_native"), "pf": ("plain,delayed_native", "delayed_native")}
 
@@ -258,6 +264,8 @@ def ragged_shapes(cfg, seed):
 
 def state_bytes(cfg):
     """Bytes of the walkers' A^{-1} state (what every timed pass streams)."""
+    if cfg["kind"] == "fig1":
+        return cfg["walkers"] * max(cfg["ns"]) ** 2 * scalar_bytes(cfg)
     if cfg["kind"] == "ragged":
         mean_n2 = float(np.mean(np.asarray(cfg["ns"], dtype=np.float64) ** 2))
         return cfg["walkers"] * mean_n2 * scalar_bytes(cfg)
@@ -273,6 +281,9 @@ def config_of(preset, cfg):
 
 def workload_name(cfg, K):
     d = cfg["dtype"].upper()
+    if cfg["kind"] == "fig1":
+        return (f"det and pf, W={cfg['walkers']} walkers/GPU, n in {list(cfg['ns'])}, rank-1 row moves / row+column "
+                f"moves, {d}: direct batched slogdet / slogpf vs LRU ratio vs LRU ratio + inverse update")
     if cfg["kind"] == "det":
         mv = "rank-1 row moves" if cfg["k"] == 1 else f"{cfg['k']}-electron row moves (k={cfg['k']})"
         var = "N(0,1)" if cfg.get("var") else "N(0,1/n)"
@@ -634,6 +645,38 @@ def cpu_baseline_ragged(cfg, seed, budget_s=15.0, max_steps=4):
     return {"value": done / tsum, "unit": "walker-updates/s", "cores": host_threads(), "kind": "oracle",
             "sample": f"plain {cfg['dtype'].upper()} chains (oracle det_lru, dense U, V) of the first {wl} walkers "
                       f"of the ragged batch x {max_steps} steps, {tsum:.1f} s"}
+
+
+def cpu_fig1(cfg, seed, budget_s=15.0, n=128):
+    """The same comparison with the oracle on the host cores at one n: its
+    from-scratch slogdet (LU, Sec. 2.1's reference values) against its
+    Sherman-Morrison step (Eq. det_inv); value = the speedup."""
+    from oracle import lru_oracle as O
+    from paper_2602_05255_gb300 import workloads
+    sub = {"walkers": 16, "n": n, "m": 2 * n, "k": 1, "dtype": "f64", "var": None, "first_rows": False}
+    Phi, occ0, slot, new = det_inputs(sub, seed, 4)
+    t_d = t_l = 0.0
+    done = 0
+    t_start = time.perf_counter()
+    for w in range(sub["walkers"]):
+        occ = occ0[w].copy()
+        Ainv = O.inv(O.slater_matrix(Phi, occ))
+        for s in range(4):
+            U, V = O.det_row_move(Phi, occ, slot[s, w], new[s, w])
+            occ2 = occ.copy()
+            occ2[slot[s, w]] = new[s, w]
+            ts = time.perf_counter()
+            O.slogdet(O.slater_matrix(Phi, occ2))
+            t_d += time.perf_counter() - ts
+            ts = time.perf_counter()
+            r, Ainv = O.det_lru(Ainv, U, V, return_update=True)
+            t_l += time.perf_counter() - ts
+            occ = occ2
+            done += 1
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return {"value": t_d / t_l, "unit": "x", "cores": host_threads(), "kind": "oracle",
+            "sample": f"oracle slogdet vs det_lru at n={n}, {done} walker-steps"}
 
 
 # --------------------------------------------------------------------------
@@ -1080,6 +1123,83 @@ def main_ragged(args, cfg, torch, L, rank, world, dist):
 
 
 # --------------------------------------------------------------------------
+# fig1: the paper's Fig. 1 scan on GB300 (context, not a target)
+# --------------------------------------------------------------------------
+def main_fig1(args, cfg, torch, L, rank, world, dist):
+    """Per n: the time of one step of W walkers for (a) the direct batched
+    slogdet / slogpf of the updated matrices (O(n^3) per walker), (b) the LRU
+    ratio alone (propose), (c) the LRU ratio with the inverse update (propose
+    + accept, plain form).  Each at warm state, CUDA events, median of a few
+    repetitions."""
+    W = cfg["walkers"]
+    reps = max(3, min(args.steps, 20))
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    table = []
+    hbm, _, _ = load_peaks()
+    for n in cfg["ns"]:
+        row = {"n": n}
+        for kind in ("det", "pf"):
+            sub = {"walkers": W, "n": n, "m": 2 * n, "k": 1, "dtype": "f64", "var": None, "first_rows": False,
+                   "delay": 0, "refresh_every": 0}
+            if kind == "det":
+                Phi, occ0, slot, new = det_inputs(sub, args.seed + n, reps + 2)
+                src = torch.tensor(Phi, device="cuda")
+            else:
+                F, occ0, slot, new = pf_inputs(sub, args.seed + n, reps + 2)
+                src = torch.tensor(F, device="cuda")
+            st = L.LowRankState(kind, W, n, k=1, dtype=torch.float64)
+            occ_d = torch.tensor(occ0, device="cuda")
+            A = st.gather_rows(src, occ_d) if kind == "det" else st.gather_pairs(src, occ_d)
+            st.init(A)
+            slot_d, new_d = torch.tensor(slot, device="cuda"), torch.tensor(new, device="cuda")
+            times = {"direct": [], "ratio": [], "ratio_and_inverse": []}
+            for s in range(reps):
+                # (a) direct: the updated matrices from scratch
+                e0, e1 = ev(), ev()
+                occ2 = occ_d.clone()
+                occ2[torch.arange(W, device="cuda"), slot_d[s].long()] = new_d[s]
+                e0.record()
+                A2 = st.gather_rows(src, occ2, A) if kind == "det" else st.gather_pairs(src, occ2, A)
+                (L.slogdet_batched if kind == "det" else L.slogpf_batched)(A2.view(W, n, n))
+                e1.record()
+                torch.cuda.synchronize()
+                times["direct"].append(e0.elapsed_time(e1))
+                # (b) ratio only and (c) ratio + inverse update
+                for key, do_accept in (("ratio", False), ("ratio_and_inverse", True)):
+                    e0, e1 = ev(), ev()
+                    e0.record()
+                    if kind == "det":
+                        V, idx = st.form_row_moves(src, occ_d, slot_d[s], new_d[s])
+                        st.propose_det(L.Operand(idx=idx, onehot_mask=1), L.Operand(dense=V))
+                    else:
+                        B, idx = st.form_pf_moves(src, occ_d, slot_d[s], new_d[s])
+                        st.propose_pf(L.Operand(dense=B, idx=idx, onehot_mask=0b10))
+                    if do_accept:
+                        st.accept()
+                        st.commit_moves(occ_d, slot_d[s], new_d[s])
+                    e1.record()
+                    torch.cuda.synchronize()
+                    times[key].append(e0.elapsed_time(e1))
+            st.close()
+            med = {k: float(np.median(v[1:] if len(v) > 1 else v)) for k, v in times.items()}
+            row[kind] = {"ms_per_step": med, "speedup_ratio_vs_direct": med["direct"] / med["ratio"],
+                         "speedup_ratio_and_inverse_vs_direct": med["direct"] / med["ratio_and_inverse"]}
+        table.append(row)
+    last = table[-1]
+    n = last["n"]
+    d_ms = last["det"]["ms_per_step"]["direct"]
+    # the direct determinant kernel at the largest n: Gauss-Jordan, n^3 FMA per walker, against the FP64 pipe
+    roof = bound_of(n * n * 8.0 * W, 2.0 * n ** 3 * W, d_ms, hbm)
+    roof["kernel"] = "direct batched slogdet (Gauss-Jordan, FP64), the O(n^3) side of the comparison"
+    line = {"metric": FIG1_METRIC, "value": last["det"]["speedup_ratio_and_inverse_vs_direct"], "unit": "x",
+            "n_gpus": world, "steps": reps, "warmup": 1, "ms_per_step": last["det"]["ms_per_step"]["ratio_and_inverse"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of("fig1", cfg), "roofline": roof, "table": table, "gpu_launches": None,
+            "paper_context": "A100-80GB, JAX: about 200x (det) and 1000x (pf) at n = 1024, 1024 matrices (Sec. 4.1)"}
+    return line
+
+
+# --------------------------------------------------------------------------
 def summary(line):
     """The line's arm against the plain arm (and the same for its Pfaffian
     arms), short enough to survive a truncated log tail."""
@@ -1124,6 +1244,8 @@ def main():
                                                       "roofline", "arms", "gpu_launches")}
     elif cfg["kind"] == "pf":
         line = main_pf(args, cfg, torch, L, rank, world, dist)
+    elif cfg["kind"] == "fig1":
+        line = main_fig1(args, cfg, torch, L, rank, world, dist)
     else:
         line = main_ragged(args, cfg, torch, L, rank, world, dist)
     line["delayed_vs_plain"] = summary(line)
@@ -1151,6 +1273,9 @@ def reference_arm(args):
         Phi, occ0, slot, new = det_inputs(cfg, args.seed, nsteps)
         cb = cpu_baseline_det(cfg, Phi, occ0, slot, new, budget_s=budget, max_steps=nsteps)
         metric = METRIC if args.config == "headline" else None
+    elif cfg["kind"] == "fig1":
+        cb = cpu_fig1(cfg, args.seed, budget_s=budget)
+        metric = FIG1_METRIC
     else:
         cb = cpu_baseline_ragged(cfg, args.seed, budget_s=budget)
         metric = RAGGED_METRIC

@@ -281,7 +281,12 @@ lru_status lru_form_row_moves(lru_handle h, const void* Phi, int32_t m, const in
  * moves from site pos[w][i] to new_site[w]; F is the m x m skew pairing
  * matrix.  Writes B (kmax = 2 vector layout): column 0 = x with
  * x_j = F(r', r_j) - F(r_i, r_j), column 1 one-hot e_i (idx_out[2w+1] = i,
- * idx_out[2w] unused); C = -J.  Uniform-n handles only. */
+ * idx_out[2w] unused); C = -J.  Handles with k = 2 move two particles at
+ * once (Sec. 3.2, the update of 2 rows and 2 columns): slot and new_site are
+ * W x 2 (distinct slots p, q; distinct unoccupied sites), B = [x, y, e_p, e_q]
+ * (kmax = 4; idx_out[4w+2] = p, idx_out[4w+3] = q, onehot_mask 0b1100) with
+ * x_j = F(r'_p, r'_j) - F(r_p, r_j) over the new sites of both particles,
+ * y_j = F(r'_q, r_j) - F(r_q, r_j), y_p = 0; C = -J.  Uniform n and k only. */
 lru_status lru_form_pf_moves(lru_handle h, const void* F, int32_t m, const int32_t* pos,
                              const int32_t* slot, const int32_t* new_site,
                              void* B_out, int32_t* idx_out);
@@ -322,6 +327,23 @@ lru_status lru_slogdet_batched_noalloc(int32_t dtype, int64_t W, int32_t n, cons
 /* slogpf of W skew matrices of even size n (Parlett-Reid with pivoting). */
 lru_status lru_slogpf_batched(int32_t dtype, int64_t W, int32_t n, const void* A,
                               double* logabs, void* sign, void* stream);
+/* Vector-Jacobian products of the two calls above (App. A.3, Eq. pf_grad; for
+ * the determinant the classical d log det A = tr(A^{-1} dA)).  Inputs: the same
+ * A (W row-major n x n), g_logabs (W doubles, dL/dlog|value|, or NULL = 0),
+ * g_sign (W scalars, dL/dsign in torch's convention for complex, or NULL; real
+ * signs are piecewise constant and get no gradient) and sign (the forward's
+ * sign / phase output, needed when g_sign is given).  Output gA (W row-major
+ * n x n, caller-owned): with c = g_logabs + i beta, beta = -Im(conj(g_sign) sign),
+ * gA = c A^{-H} (determinant; real: g_logabs A^{-T}) or (c / 2) times the
+ * conjugate transpose of the skew part of A^{-1} (Pfaffian: the gradient with
+ * respect to A through its skew projection).  The inverses are formed in FP64
+ * / complex128 (Gauss-Jordan) in a workspace allocated on the stream for the
+ * call.  A singular A gives non-finite gradients.  W <= INT32_MAX, n <= 2048,
+ * n even for the Pfaffian. */
+lru_status lru_slogdet_backward(int32_t dtype, int64_t W, int32_t n, const void* A, const double* g_logabs,
+                                const void* g_sign, const void* sign, void* gA, void* stream);
+lru_status lru_slogpf_backward(int32_t dtype, int64_t W, int32_t n, const void* A, const double* g_logabs,
+                               const void* g_sign, const void* sign, void* gA, void* stream);
 
 /* ---- profiling (CUDA events on the handle's stream) ----------------------- */
 

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblrugb.so")
+LIB_DEBUG = os.path.join(HERE, "liblrugb_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 # (source, object, extra defines): the kernel file is split by dtype
@@ -48,18 +49,24 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(p) for p in paths if os.path.isfile(p))
 
 
-def build(verbose: bool = False) -> str:
+def build(verbose: bool = False, debug: bool = False) -> str:
+    """Compiles (the changed units of) liblrugb.so, or with debug=True
+    liblrugb_debug.so (-DLRU_DEBUG: device-side index checks that record a
+    sticky error, canary-guarded handle allocations)."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = os.path.join(BUILD, "debug") if debug else BUILD
+    lib = LIB_DEBUG if debug else LIB
+    extra = ["-DLRU_DEBUG"] if debug else []
+    os.makedirs(bdir, exist_ok=True)
     dep = _deps_mtime()
     jobs = []
     objs = []
     for src_name, obj_name, defs in UNITS:
         src = os.path.join(CSRC, src_name)
-        obj = os.path.join(BUILD, obj_name)
+        obj = os.path.join(bdir, obj_name)
         objs.append(obj)
         if not os.path.exists(obj) or os.path.getmtime(obj) < dep:
-            jobs.append([nvcc, *ARCH, *FLAGS, *defs, "-c", src, "-o", obj])
+            jobs.append([nvcc, *ARCH, *FLAGS, *extra, *defs, "-c", src, "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
     for cmd, r in zip(jobs, results):
@@ -67,14 +74,15 @@ def build(verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed ({' '.join(cmd[-3:])}):\n{r.stdout}\n{r.stderr}")
         if verbose and (r.stdout or r.stderr):
             print(r.stdout, r.stderr)
-    if jobs or not os.path.exists(LIB):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-cudart", "shared",
+    if jobs or not os.path.exists(lib):
+        cmd = [nvcc, *ARCH, "-shared", "-o", lib, *objs, "-cudart", "shared",
                "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True))
+    import sys
+    print(build(verbose=True, debug="--debug" in sys.argv))

@@ -16,6 +16,8 @@
 // product  g * conj(J)  that PyTorch's autograd expects for holomorphic maps.
 // The delayed state never materialises A^{-1}: Y is recomputed from A_0^{-1}
 // and the stored slots, Y = V A_0^{-1} - (V P) Q^T.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -295,7 +297,49 @@ void launch_scatter_rows(const DevLayout& L, const T* gA, const int* rows, int m
     k_scatter_rows<T><<<grid, 256, 0, st>>>(L, gA, rows, m, gPhi, err);
 }
 
+// Gradient of the outputs (sign or phase s, log|value|) of the batched
+// slogdet / slogpf: with t = tr(A^{-1} dA), d log|det A| = Re t and
+// d s = i s Im t, so for a loss L with dL/dlog|.| = g_l and dL/ds = g_s (torch's
+// convention for complex) dL = Re(conj(c) t), c = g_l + i beta,
+// beta = -Im(conj(g_s) s), and grad_A = c A^{-H} (real: g_l A^{-T}).  The
+// Pfaffian has log pf = (1/2) log det of the skew part (App. A.3, Eq.
+// pf_grad): grad_A = (c / 2) (skew part of A^{-1})^H.  Ginv: the column-major
+// inverses, Ginv[w][l n + j] = (A_w^{-1})_{jl}, so (A^{-H})_{ij} is
+// conj(Ginv[w][i n + j]).
+template <typename T>
+__global__ void k_slog_grad(int W, int n, bool pf, const T* Ginv, const double* g_l, const T* g_s, const T* sign,
+                            T* gA) {
+    const long long nn = (long long)n * n, total = nn * W;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(e / nn);
+        const long long r = e - (long long)w * nn;
+        const int i = (int)(r / n), j = (int)(r - (long long)i * n);
+        const T* G = Ginv + (long long)w * nn;
+        T c = make_real<T>(g_l ? g_l[w] : 0.0);
+        if constexpr (traits<T>::is_complex) {
+            if (g_s) {
+                const T q = s_conj(g_s[w]) * sign[w];
+                c.im = -q.im;
+            }
+        }
+        T v = G[(long long)i * n + j];
+        if (pf) v = s_half(s_half(v - G[(long long)j * n + i]));   // (1/2) of the skew part
+        gA[e] = c * s_conj(v);
+    }
+}
+
+template <typename T>
+void launch_slog_grad(int W, int n, bool pf, const T* Ginv, const double* g_l, const T* g_s, const T* sign, T* gA,
+                      cudaStream_t st) {
+    const long long total = (long long)n * n * W;
+    const int grid = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+    k_slog_grad<T><<<grid, 256, 0, st>>>(W, n, pf, Ginv, g_l, g_s, sign, gA);
+}
+
 #define LRU_INST_A(T)                                                                                        \
+    template void launch_slog_grad<T>(int, int, bool, const T*, const double*, const T*, const T*, T*,        \
+                                      cudaStream_t);                                                          \
     template void launch_backward<T>(bool, bool, const DevLayout&, const DevState<T>&, const DevOperand&,     \
                                      const T*, const T*, T*, T*, T*, T*, T*, cudaStream_t);                   \
     template void launch_backward_logvalue<T>(bool, bool, const DevLayout&, const DevState<T>&, const T*, T*, \

@@ -164,9 +164,19 @@ template <typename T> __device__ T block_sum(T v, T* sbuf) {
 }
 
 // sticky error codes written to the handle's device error word
-enum : int { DEV_ERR_NONE = 0, DEV_ERR_TIMEOUT = 1, DEV_ERR_INDEX = 2, DEV_ERR_TMEM = 3 };
+enum : int { DEV_ERR_NONE = 0, DEV_ERR_TIMEOUT = 1, DEV_ERR_INDEX = 2, DEV_ERR_TMEM = 3, DEV_ERR_CANARY = 4 };
 LRU_D void set_dev_error(int* flag, int code) {
     if (flag) atomicCAS(flag, 0, code);
 }
+
+// Debug build (-DLRU_DEBUG): checks of work-item indices against the sizes
+// they address.  A failed check records DEV_ERR_INDEX in the sticky error word
+// and the caller skips the work (no trap, no out-of-range access); `cond` must
+// be the same for every thread of the CTA.  Release builds compile nothing.
+#ifdef LRU_DEBUG
+#define LRU_DEBUG_OK(cond, err) ((cond) ? true : (set_dev_error((err), DEV_ERR_INDEX), false))
+#else
+#define LRU_DEBUG_OK(cond, err) true
+#endif
 
 }  // namespace lru

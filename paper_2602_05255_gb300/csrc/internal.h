@@ -192,6 +192,10 @@ void launch_backward_logvalue(bool pf, bool delayed, const DevLayout& L, const D
                               cudaStream_t st);
 template <typename T>
 void launch_log_ratio(int W, const T* ratio, T* out, cudaStream_t st);
+// gradient of (sign, log|det|) or (phase, log|pf|) from the column-major inverses
+template <typename T>
+void launch_slog_grad(int W, int n, bool pf, const T* Ginv, const double* g_l, const T* g_s, const T* sign, T* gA,
+                      cudaStream_t st);
 template <typename T>
 void launch_scatter_rows(const DevLayout& L, const T* gA, const int* rows, int m, T* gPhi, int* err, cudaStream_t st);
 

@@ -593,10 +593,12 @@ __device__ void accept_item(const int4 it, const DevLayout L, const DevState<T> 
                             const uint8_t* mask) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int w = it.x;
+    if (!LRU_DEBUG_OK(w >= 0 && w < L.W, S.err)) return;
     if (mask && !mask[w]) return;
     if (S.pst[w] != 0) return;
     // KKS > 0: the rank is a compile-time constant (register arrays), else runtime
     const int n = L.nw(w), kk = KKS > 0 ? KKS : L.kv(w);
+    if (!LRU_DEBUG_OK(it.y >= 0 && it.y <= it.z && it.z <= n, S.err)) return;
     const long long vo = L.vo(w);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // X and the dense V vectors are staged in shared memory when they fit
@@ -883,6 +885,7 @@ __global__ void __launch_bounds__(PT, 2) k_accept_delayed_warp_df(DevLayout L, D
     const int np = n >> 1;   // n is even
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int l0 = blockIdx.y * DF_CPB;
+    if (!LRU_DEBUG_OK((n & 1) == 0 && np <= 32 * NP2 && l0 < n && cu < Kc, S.err)) return;
     const int ncol = min(n - l0, DF_CPB);
     const double* vb = vec_ptr<double>(V, L, w, 0, n);
     for (int p = threadIdx.x; p < 32 * NP2; p += PT) {
@@ -1165,6 +1168,7 @@ __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int 
     constexpr int LD = CH + 1;
     const int n = L.nw(w), kk = L.kv(w);
     const int cu = tau * kk, Kc = L.Kc;
+    if (!LRU_DEBUG_OK(tJ >= 0 && tL >= 0 && 32 * tJ < n && 32 * tL < n && cu <= Kc, S.err)) return;
     const long long vo = L.vo(w);
     T* Gw = S.G + L.mo(w);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
@@ -1365,6 +1369,7 @@ __global__ void __launch_bounds__(PT) k_step(DevLayout L, DevState<T> S, DevOper
         if (item >= total) break;
         if (item < L.W) {
             const int w = ctl.order[item];
+            if (!LRU_DEBUG_OK(w >= 0 && w < L.W, S.err)) continue;
             if constexpr (DEL) qtu_block<T>(w, L, S, U);
             propose_walker<T, PF, DEL>(w, L, S, U, V, C, ratio_out, st_out);
             __syncthreads();
@@ -1401,6 +1406,7 @@ __global__ void __launch_bounds__(PT) k_step(DevLayout L, DevState<T> S, DevOper
         } else {
             const int2 fi = ctl.flush_items[item - L.W - nacc];
             const int w = fi.x, tL = fi.y;
+            if (!LRU_DEBUG_OK(w >= 0 && w < L.W && tL >= 0 && 32 * tL < L.nw(w), S.err)) continue;
             if (threadIdx.x == 0) {
                 s_ok = bounded_acquire_wait(&ctl.fin[w], 1, STEP_WAIT_POLLS, S.err) ? 1 : 0;
                 s_tau = s_ok ? *(volatile const int*)&S.tau[w] : 0;
@@ -1576,6 +1582,37 @@ __global__ void k_form_pf_moves(DevLayout L, const T* F, int m, const int* pos, 
     if (threadIdx.x == 0) {
         idx[2 * w] = -1;
         idx[2 * w + 1] = ok ? i : -1;
+    }
+}
+
+// Two particles p, q of every walker move to new sites at once (Sec. 3.2,
+// the update of 2 rows and 2 columns): B = [x, y, e_p, e_q] (C = -J),
+// x_j = F(r'_p, r'_j) - F(r_p, r_j) with both new sites, y_j = F(r'_q, r_j) -
+// F(r_q, r_j), y_p = 0, so that entry (p, q) of the change is x_q - y_p.
+// slot, newsite: W x 2; Bout: W x 4 vectors of n (slots 0, 1 dense); idx: W x 4.
+template <typename T>
+__global__ void k_form_pf_moves2(DevLayout L, const T* F, int m, const int* pos, const int* slot,
+                                 const int* newsite, T* Bout, int* idx) {
+    const int w = blockIdx.x, n = L.n_uni;
+    const int p = slot[2 * w], q = slot[2 * w + 1];
+    const int sp = newsite[2 * w], sq = newsite[2 * w + 1];
+    const bool okpq = p >= 0 && p < n && q >= 0 && q < n && p != q;
+    const int rp = okpq ? pos[(long long)w * n + p] : 0, rq = okpq ? pos[(long long)w * n + q] : 0;
+    const bool ok = okpq && sp >= 0 && sp < m && sq >= 0 && sq < m && rp >= 0 && rp < m && rq >= 0 && rq < m;
+    T* x = Bout + (long long)w * 4 * n;
+    T* y = x + n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int rj = pos[(long long)w * n + j];
+        const bool okj = ok && rj >= 0 && rj < m;
+        const int rj_new = j == p ? sp : (j == q ? sq : rj);
+        x[j] = okj ? (F[(long long)sp * m + rj_new] - F[(long long)rp * m + rj]) : s_zero(T());
+        y[j] = (okj && j != p) ? (F[(long long)sq * m + rj] - F[(long long)rq * m + rj]) : s_zero(T());
+    }
+    if (threadIdx.x == 0) {
+        idx[4 * w] = -1;
+        idx[4 * w + 1] = -1;
+        idx[4 * w + 2] = ok ? p : -1;
+        idx[4 * w + 3] = ok ? q : -1;
     }
 }
 
@@ -1802,7 +1839,8 @@ void launch_form_row_moves(const DevLayout& L, const T* Phi, int m, const int* o
 template <typename T>
 void launch_form_pf_moves(const DevLayout& L, const T* F, int m, const int* pos, const int* slot,
                           const int* newsite, T* Bout, int* idx, cudaStream_t st) {
-    k_form_pf_moves<T><<<L.W, 256, 0, st>>>(L, F, m, pos, slot, newsite, Bout, idx);
+    if (L.kk == 4) k_form_pf_moves2<T><<<L.W, 256, 0, st>>>(L, F, m, pos, slot, newsite, Bout, idx);
+    else k_form_pf_moves<T><<<L.W, 256, 0, st>>>(L, F, m, pos, slot, newsite, Bout, idx);
 }
 
 #if !defined(LRU_INST_DTYPE) || defined(LRU_INST_PRIMARY)

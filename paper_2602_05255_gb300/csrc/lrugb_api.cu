@@ -32,6 +32,7 @@ namespace {
 constexpr int MAXKK = 16;
 constexpr int MAXN = 2048;
 constexpr int MAXKC = 64;
+constexpr size_t CANARY_BYTES = 256;   // debug build: guard zone after each region of a handle's allocation
 
 size_t dtype_size(int d) {
     switch (d) {
@@ -109,6 +110,8 @@ struct lru_ctx {
     // adjoint workspace (allocated on first use)
     void* bws = nullptr;
     int n_sm = 148;
+    // debug build: offsets of the guard zones between the regions of the allocation
+    std::vector<size_t> canaries;
 
     DevLayout layout() const {
         DevLayout L;
@@ -217,7 +220,11 @@ const char* lru_status_string(lru_status s) {
     return "unknown status";
 }
 
-const char* lru_version(void) { return "lrugb 0.1.0 sm_103a"; }
+#ifdef LRU_DEBUG
+const char* lru_version(void) { return "lrugb 0.2.0 sm_103a debug"; }
+#else
+const char* lru_version(void) { return "lrugb 0.2.0 sm_103a"; }
+#endif
 
 lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     LRU_RANGE();
@@ -350,7 +357,19 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
     const bool tc = delayed && cfg->flush != LRU_FLUSH_NATIVE && cfg->flush != LRU_FLUSH_DF &&
                     cfg->flush != LRU_FLUSH_SPLIT;
     size_t off = 0;
+#ifdef LRU_DEBUG
+    // every region is followed by a guard zone of CANARY_BYTES bytes of 0xA5
+    // that lru_check_device_error verifies
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off = align_up(off + b);
+        h->canaries.push_back(off);
+        off = align_up(off + CANARY_BYTES);
+        return o;
+    };
+#else
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b); return o; };
+#endif
     const size_t oG = take((size_t)h->sum_n2 * sz);
     const size_t oP = delayed ? take((size_t)h->sum_n * h->Kc * sz) : 0;
     const size_t oQ = delayed ? take((size_t)h->sum_n * h->Kc * sz) : 0;
@@ -431,6 +450,10 @@ lru_status lru_create(const lru_config* cfg, lru_handle* out) {
          cudaMemcpy(h->d_fitems, fitems.data(), fitems.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemcpy(h->d_nflush_w, nflush_w.data(), h->W * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
         s = LRU_ERR_CUDA;
+#ifdef LRU_DEBUG
+    for (size_t c : h->canaries)
+        if (s == LRU_OK && cudaMemset(h->base + c, 0xA5, CANARY_BYTES) != cudaSuccess) s = LRU_ERR_CUDA;
+#endif
     if (s != LRU_OK) {
         cudaGetLastError();
         cudaFree(h->base);
@@ -814,6 +837,16 @@ lru_status lru_check_device_error(lru_handle h) {
     int e = 0;
     CK(cudaMemcpy(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) CK(cudaMemset(h->err, 0, sizeof(int)));
+#ifdef LRU_DEBUG
+    // the guard zones must still hold their pattern: a write past the end of a
+    // region of the state (or of the scratch) lands in one of them
+    std::vector<unsigned char> guard(CANARY_BYTES);
+    for (size_t c : h->canaries) {
+        CK(cudaMemcpy(guard.data(), h->base + c, CANARY_BYTES, cudaMemcpyDeviceToHost));
+        for (unsigned char v : guard)
+            if (v != 0xA5 && !e) e = DEV_ERR_CANARY;
+    }
+#endif
     if (e == DEV_ERR_TIMEOUT) return LRU_ERR_TIMEOUT;
     if (e) return LRU_ERR_CUDA;
     return LRU_OK;
@@ -847,7 +880,7 @@ lru_status lru_form_pf_moves(lru_handle h, const void* F, int32_t m, const int32
                              const int32_t* new_site, void* B_out, int32_t* idx_out) {
     LRU_RANGE();
     if (!h || !F || !pos || !slot || !new_site || !B_out || !idx_out || m < 1) return LRU_ERR_ARG;
-    if (!h->pf || h->n_uni <= 0 || h->kk != 2) return LRU_ERR_ARG;
+    if (!h->pf || h->n_uni <= 0 || (h->kk != 2 && h->kk != 4) || h->d_kv) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     DevLayout L = h->layout();
     h->launches += 1;
@@ -864,7 +897,7 @@ lru_status lru_commit_moves(lru_handle h, int32_t* occ, const int32_t* slot, con
     if (h->n_uni <= 0) return LRU_ERR_ARG;
     CK(cudaSetDevice(h->device));
     h->launches += 1;
-    launch_commit_moves(h->W, h->n_uni, h->pf ? 1 : h->kk, occ, slot, new_row, mask, h->pst, h->stream);
+    launch_commit_moves(h->W, h->n_uni, h->pf ? h->kk / 2 : h->kk, occ, slot, new_row, mask, h->pst, h->stream);
     return cuda_check();
 }
 
@@ -1015,6 +1048,57 @@ lru_status lru_slogdet_batched(int32_t dtype, int64_t W, int32_t n, const void* 
                                void* stream) {
     LRU_RANGE();
     return batched_dense(false, dtype, W, n, A, logabs, sign, stream);
+}
+
+static lru_status slog_backward(bool pf, int32_t dtype, int64_t W, int32_t n, const void* A, const double* g_logabs,
+                                const void* g_sign, const void* sign, void* gA, void* stream) {
+    if (W < 1 || W > (int64_t)INT32_MAX || n < 1 || n > MAXN || !A || !gA || dtype_size(dtype) == 0) return LRU_ERR_ARG;
+    if (pf && (n & 1)) return LRU_ERR_ARG;
+    if (g_sign && !sign) return LRU_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 148;
+    CK(cudaGetDevice(&dev));
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { cudaGetLastError(); nsm = 148; }
+    const int nws = (int)std::min<int64_t>(W, 2 * nsm);
+    const size_t sz = dtype_size(dtype), nn = (size_t)n * n;
+    // the inverses (W n^2), the Gauss-Jordan slots (nws n^2) and the per-walker status
+    void* buf = nullptr;
+    CK(cudaMallocAsync(&buf, align_up((size_t)W * nn * sz) + align_up((size_t)nws * nn * sz) + (size_t)W * sizeof(int),
+                       st));
+    unsigned char* b = (unsigned char*)buf;
+    void* Ginv = b;
+    void* ws = b + align_up((size_t)W * nn * sz);
+    int* pst = (int*)(b + align_up((size_t)W * nn * sz) + align_up((size_t)nws * nn * sz));
+    DevLayout L{};
+    L.W = (int)W;
+    L.n_uni = n;
+    L.n_max = n;
+    L.kk = 1;
+    lru_ctx tmp;
+    tmp.dtype = dtype;
+    lru_ctx* h = &tmp;
+    LRU_DISPATCH(h, {
+        DevState<T> S{};
+        S.G = (T*)Ginv;
+        S.pst = pst;
+        launch_refresh<T>(false, false, L, S, (const T*)A, nullptr, (T*)ws, nws, nullptr, false, st);
+        launch_slog_grad<T>((int)W, n, pf, (const T*)Ginv, g_logabs, (const T*)g_sign, (const T*)sign, (T*)gA, st);
+    });
+    lru_status s = cuda_check();
+    cudaFreeAsync(buf, st);
+    return s;
+}
+
+lru_status lru_slogdet_backward(int32_t dtype, int64_t W, int32_t n, const void* A, const double* g_logabs,
+                                const void* g_sign, const void* sign, void* gA, void* stream) {
+    LRU_RANGE();
+    return slog_backward(false, dtype, W, n, A, g_logabs, g_sign, sign, gA, stream);
+}
+
+lru_status lru_slogpf_backward(int32_t dtype, int64_t W, int32_t n, const void* A, const double* g_logabs,
+                               const void* g_sign, const void* sign, void* gA, void* stream) {
+    LRU_RANGE();
+    return slog_backward(true, dtype, W, n, A, g_logabs, g_sign, sign, gA, stream);
 }
 
 lru_status lru_slogpf_batched(int32_t dtype, int64_t W, int32_t n, const void* A, double* logabs, void* sign,

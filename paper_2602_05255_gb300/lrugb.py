@@ -19,7 +19,10 @@ from typing import Optional
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblrugb.so")
+# LRUGB_DEBUG=1 loads the debug build (device-side index checks that record a
+# sticky error instead of reading out of range, canary-guarded state buffers)
+DEBUG = os.environ.get("LRUGB_DEBUG", "") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "liblrugb_debug.so" if DEBUG else "liblrugb.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -99,6 +102,8 @@ _SIGS = {
     "lru_slogdet_batched": [_i32, _i64, _i32, _vp, _vp, _vp, _vp],
     "lru_slogpf_batched": [_i32, _i64, _i32, _vp, _vp, _vp, _vp],
     "lru_slogdet_batched_noalloc": [_i32, _i64, _i32, _vp, _vp, _vp, _vp],
+    "lru_slogdet_backward": [_i32, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
+    "lru_slogpf_backward": [_i32, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -425,8 +430,9 @@ class LowRankState:
     def form_pf_moves(self, F, pos, slot, new_site, B_out=None, idx_out=None):
         self._bind()
         n = self.n_list[0]
-        B_out = torch.empty(self.W, 2, n, dtype=self.dtype, device=self.device) if B_out is None else B_out
-        idx_out = torch.empty(self.W, 2, dtype=torch.int32, device=self.device) if idx_out is None else idx_out
+        kk = self.kmax        # 2 (one particle) or 4 (two particles at once)
+        B_out = torch.empty(self.W, kk, n, dtype=self.dtype, device=self.device) if B_out is None else B_out
+        idx_out = torch.empty(self.W, kk, dtype=torch.int32, device=self.device) if idx_out is None else idx_out
         _check(_lib.lru_form_pf_moves(self._h, _ptr(F), F.shape[0], _ptr(pos), _ptr(slot), _ptr(new_site),
                                       _ptr(B_out), _ptr(idx_out)), "lru_form_pf_moves")
         return B_out, idx_out
@@ -482,6 +488,45 @@ def slogpf_batched(A: torch.Tensor):
     _check(_lib.lru_slogpf_batched(_DTYPES[A.dtype], W, n, _ptr(A), _ptr(logabs), _ptr(sign), _stream()),
            "lru_slogpf_batched")
     return sign, logabs
+
+
+class _SlogBatched(torch.autograd.Function):
+    """(sign, log|det A|) or (sign, log|pf A|) of a batch, differentiable: the
+    forward is lru_slogdet_batched / lru_slogpf_batched, the backward
+    lru_slogdet_backward / lru_slogpf_backward (App. A.3)."""
+
+    @staticmethod
+    def forward(ctx, A, pf):
+        A = A.contiguous()
+        sign, logabs = (slogpf_batched if pf else slogdet_batched)(A)
+        ctx.save_for_backward(A, sign)
+        ctx.pf = pf
+        if not A.is_complex():
+            ctx.mark_non_differentiable(sign)
+        return sign, logabs
+
+    @staticmethod
+    def backward(ctx, g_sign, g_logabs):
+        A, sign = ctx.saved_tensors
+        W, n = A.shape[0], A.shape[-1]
+        gA = torch.empty_like(A)
+        g_l = g_logabs.contiguous().to(torch.float64) if g_logabs is not None else None
+        g_s = g_sign.contiguous() if (g_sign is not None and A.is_complex()) else None
+        f = _lib.lru_slogpf_backward if ctx.pf else _lib.lru_slogdet_backward
+        _check(f(_DTYPES[A.dtype], W, n, _ptr(A), _ptr(g_l), _ptr(g_s), _ptr(sign), _ptr(gA), _stream()),
+               "lru_slog_backward")
+        return gA, None
+
+
+def slogdet(A: torch.Tensor):
+    """Differentiable (sign, log|det|) of W matrices (W, n, n) on the device."""
+    return _SlogBatched.apply(A, False)
+
+
+def slogpf(A: torch.Tensor):
+    """Differentiable (sign, log|pf|) of W skew matrices (W, n, n); the
+    gradient is taken through the skew projection (A - A^T) / 2 (App. A.3)."""
+    return _SlogBatched.apply(A, True)
 
 
 # ---------------------------------------------------------------------------

@@ -201,6 +201,51 @@ def test_pf_1024_walkers_n256(case):
         assert abs(logabs[q] - l1) <= 1e-9 * max(1.0, abs(l1))
 
 
+@pytest.mark.parametrize("delay", [0, 8])
+def test_pf_two_particle_moves_1024_walkers_n256(delay):
+    """C3's walkers and pairing matrix with two particles moved at once per
+    step (Sec. 3.2, 2 rows and 2 columns; B n x 4, C = -J), plain and
+    delayed (K = 8: 32 slot columns), sampled walkers against the oracle."""
+    L = lrugb()
+    W, n, m, steps = 1024, 256, 512, 96
+    seed = 3
+    G = workloads.pairing_generator(seed, m, 1.0 / n)
+    F = G - G.T
+    pos0 = workloads.initial_occupation(seed + 1, W, m, n)
+    slot, new = workloads.multi_move_sequence(seed + 12, pos0, m, steps, 2)
+    st = L.LowRankState("pf", W, n, k=2, dtype=torch.float64, delay=delay)
+    F_d, pos_d = tdev(F), tdev(pos0)
+    st.init(st.gather_pairs(F_d, pos_d))
+    sample = [0, 700, W - 1]
+    ratios = np.zeros((steps, len(sample)))
+    slot_d, new_d = tdev(slot), tdev(new)
+    for s in range(steps):
+        B, idx = st.form_pf_moves(F_d, pos_d, slot_d[s], new_d[s])
+        r, _ = st.propose_pf(L.Operand(dense=B, idx=idx, onehot_mask=0b1100))
+        st.accept()
+        st.commit_moves(pos_d, slot_d[s], new_d[s])
+        ratios[s] = r[sample].cpu().numpy()
+    inv = st.inverse()[sample].cpu().numpy()
+    st.check_device_error()
+    for q_, w in enumerate(sample):
+        pos = pos0[w].copy()
+        car = O.init_pf_carrier(O.pairing_matrix(F, pos), delay) if delay else None
+        Ainv = O.skew_part(O.inv(O.pairing_matrix(F, pos)))
+        chain, exact = [], []
+        for s in range(steps):
+            (p, q), (sp, sq) = slot[s, w], new[s, w]
+            B, C = O.pf_two_particle_move(F, pos, p, q, sp, sq)
+            exact.append(exact_pf_ratio(O.pairing_matrix(F, pos), B, C))
+            if delay:
+                chain.append(O.pf_lru_delayed(car, B, C))
+            else:
+                r, Ainv = O.pf_lru(Ainv, B, C, return_update=True)
+                chain.append(r)
+            pos[p], pos[q] = sp, sq
+        check_ratios(ratios[:, q_], chain, exact, what=("two-particle", delay, w), ceiling=CEIL_CHAIN)
+        assert fro_rel(inv[q_], np.linalg.inv(O.pairing_matrix(F, pos))) <= 1e-9
+
+
 # C4 arms: flush, and the asserted bounds on the relative ratio error against
 # the FP64 oracle chain (median, p99, p99.9, max; 8 walkers x 256 steps) and
 # on the Frobenius drift of A^{-1} after 64 updates (None: reported, not

@@ -119,3 +119,50 @@ def test_slogpf_batched(cplx):
     M = np.array([[0, 2, 3, 5], [-2, 0, 7, 11], [-3, -7, 0, 13], [-5, -11, -13, 0]], float)[None]
     sgn, logabs = L.slogpf_batched(tdev(M))
     assert sgn.item() * np.exp(logabs.item()) == pytest.approx(28.0, rel=1e-14)
+
+
+@pytest.mark.parametrize("delay", [0, 4])
+def test_two_particle_moves_match_oracle(delay):
+    # two particles of every walker move at once (Sec. 3.2, 2 rows and 2
+    # columns): operands built on the device, plain (skew rank-4 accept) and
+    # delayed, against the oracle's chain on the same moves
+    L = lrugb()
+    from paper_2602_05255_gb300 import workloads
+    W, n, m, steps = 4, 40, 96, 24
+    G = workloads.pairing_generator(88 + delay, m, 1.0 / n)
+    F = G - G.T
+    pos0 = workloads.initial_occupation(89 + delay, W, m, n)
+    slot, new = workloads.multi_move_sequence(90 + delay, pos0, m, steps, 2)
+    st = L.LowRankState("pf", W, n, k=2, dtype=torch.float64, delay=delay)
+    F_d, pos_d = tdev(F), tdev(pos0)
+    st.init(st.gather_pairs(F_d, pos_d))
+    ratios = []
+    for s in range(steps):
+        B, idx = st.form_pf_moves(F_d, pos_d, tdev(slot[s]), tdev(new[s]))
+        r, status = st.propose_pf(L.Operand(dense=B, idx=idx, onehot_mask=0b1100))
+        assert (status.cpu().numpy() == 0).all()
+        st.accept()
+        st.commit_moves(pos_d, tdev(slot[s]), tdev(new[s]))
+        ratios.append(r.cpu().numpy())
+    ratios = np.array(ratios)
+    inv = st.inverse().cpu().numpy()
+    pos_end = pos_d.cpu().numpy()
+    for w in range(W):
+        pos = pos0[w].copy()
+        A = O.pairing_matrix(F, pos)
+        car = O.init_pf_carrier(A, delay) if delay else None
+        Ainv = O.skew_part(O.inv(A))
+        chain, exact = [], []
+        for s in range(steps):
+            (p, q), (sp, sq) = slot[s, w], new[s, w]
+            B, C = O.pf_two_particle_move(F, pos, p, q, sp, sq)
+            exact.append(O.pf_ratio_direct(O.pairing_matrix(F, pos), B, C))
+            if delay:
+                chain.append(O.pf_lru_delayed(car, B, C))
+            else:
+                r, Ainv = O.pf_lru(Ainv, B, C, return_update=True)
+                chain.append(r)
+            pos[p], pos[q] = sp, sq
+        check_ratios(ratios[:, w], chain, exact, what=(delay, w))
+        assert np.array_equal(pos, pos_end[w])
+        assert fro_rel(inv[w], O.inv(O.pairing_matrix(F, pos))) <= 1e-9
