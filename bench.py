@@ -100,7 +100,7 @@ ARMS = {
 # Pfaffian arms: name -> (delay, arithmetic of the propose's pass over A^{-1}, flush)
 PF_ARMS = {
     "plain": (0, "native", "native"),               # exactly skew rank-2 accept (Eq. pf_inv)
-    "delayed": (None, "native", "split"),           # split-product flush + skew projection (Eq. pf_delayed_Ainv)
+    "delayed": (None, "native", "split"),           # split-product flush, lower triangle mirrored (Eq. pf_delayed_Ainv)
     "delayed_native": (None, "native", "native"),   # FP64 skew flush
     "delayed_dfflush": (None, "native", "df"),      # double-float skew flush
     "delayed_df": (None, "df", "df"),               # double-float pass and flush

@@ -81,8 +81,8 @@ typedef enum {
     LRU_FLUSH_DF = 5,       /* F64 only: double-float products on the FP32 pipe (about 1e-14 relative) */
     LRU_FLUSH_SPLIT = 6     /* F64, uniform n % 128 == 0 (n <= 2048), K*k <= 64 (Pfaffian: K*2k): exact
                                BF16 split products on the tensor cores with FP64 recombination (the
-                               rounding of an FP64 update); the Pfaffian result is then projected onto
-                               its skew part, lower triangle the exact negative of the upper */
+                               rounding of an FP64 update); for the Pfaffian the upper triangle of the
+                               result is kept and the lower one written as its exact negative */
 } lru_flush;
 
 /* Arithmetic of the streaming passes over A^{-1} for F64 handles. */

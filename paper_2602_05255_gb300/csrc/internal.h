@@ -155,8 +155,8 @@ void launch_oz_drift_store(int W, int n, const DevLayout& L, const DevState<doub
 // tau >= K, or force && tau > 0 (their go flags stay set for launch_skew_project)
 bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, const double* Q, double sgnQ,
                         const int* tau, const uint8_t* force, const OzWork& Z, int* err, cudaStream_t st);
-// A_0^{-1} of the walkers with go[w] set := its skew part, lower triangle the
-// exact negative of the upper (after the Pfaffian split-product flush; n % 32 == 0)
+// A_0^{-1} of the walkers with go[w] set: the lower triangle := the exact
+// negative of the upper, diagonal 0 (after the Pfaffian split-product flush; n % 32 == 0)
 void launch_skew_project(int W, int n, double* G, const uint8_t* go, cudaStream_t st);
 // hook(ctx, class, begin) brackets the panel (class 4) and update (class 5) launches
 bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const DevState<double>& S,

@@ -716,7 +716,7 @@ static lru_status do_flush(lru_handle h, const uint8_t* force) {
         Z.M = (double*)h->G;
         h->launches += 4;   // flush flags, column balance, two slicings, GEMM (+ finish counted above)
         // determinant: A_0^{-1} -= P Q^T (Eq. delayed_Ainv); Pfaffian: A_0^{-1} += P Q^T
-        // (Eq. pf_delayed_Ainv), then projected back onto an exactly skew matrix
+        // (Eq. pf_delayed_Ainv), then the lower triangle mirrored from the upper
         if (!launch_flush_split(h->W, h->n_uni, h->K, h->Kc, h->kk, (const double*)h->P, (const double*)h->Q,
                                 h->pf ? 1.0 : -1.0, h->tau, force, Z, h->err, h->stream)) {
             prof_end(h, LRU_PROF_FLUSH);

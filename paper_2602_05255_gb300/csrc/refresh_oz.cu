@@ -557,13 +557,16 @@ bool launch_flush_split(int W, int n, int K, int Kc, int kk, const double* P, co
     return true;
 }
 
-// Projection of the flushed walkers' A_0^{-1} onto its skew part, after the
-// Pfaffian split-product flush A_0^{-1} += P Q^T: the exact products of the
-// rounded slots (P = a M^{-1}, Q = a) are skew only up to that rounding, and
-// the upper entry becomes (G_jl - G_lj) / 2, the lower one its exact negative
-// (sign flip), the diagonal zero.  One CTA per (walker, 32 x 32 upper tile).
+// Exact skew symmetry of the flushed walkers' A_0^{-1}, after the Pfaffian
+// split-product flush A_0^{-1} += P Q^T: the product of the rounded slots
+// (P = a M^{-1}, Q = a) is skew only up to that rounding, so the upper
+// triangle (each entry one rounding of an exact product) is kept and the
+// lower triangle is written as its exact negative (a sign flip, no FP64
+// arithmetic), the diagonal as zero -- the same rule as the FP64 skew flush.
+// Reads the upper half, writes the lower half.  One CTA per (walker, 32 x 32
+// upper tile).
 __global__ void __launch_bounds__(256) k_skew_project(int n, double* G, const uint8_t* go) {
-    __shared__ double sU[32][33], sL[32][33];
+    __shared__ double sU[32][33];
     const int w = blockIdx.y;
     if (!go[w]) return;
     const int nt = n / 32;
@@ -572,28 +575,29 @@ __global__ void __launch_bounds__(256) k_skew_project(int n, double* G, const ui
     const int j0 = 32 * r, l0 = 32 * (r + rem);
     double* Gw = G + (long long)w * n * n;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    // sU[l][j] = G(j0 + j, l0 + l) at Gw[l * n + j]; sL[j][l] = G(l0 + l, j0 + j) at Gw[j * n + l]
+    // sU[l][j] = G(j0 + j, l0 + l), stored at Gw[(l0 + l) * n + j0 + j]
     for (int q = 0; q < 4; ++q) {
         const int a = ty + 8 * q;
         sU[a][tx] = Gw[(long long)(l0 + a) * n + j0 + tx];
-        sL[a][tx] = Gw[(long long)(j0 + a) * n + l0 + tx];
     }
     __syncthreads();
-    for (int q = 0; q < 4; ++q) {
-        const int a = ty + 8 * q;   // l within the tile, tx = j
-        double v;
-        if (r == r + rem && tx == a) v = 0.0;
-        else if (r == r + rem && tx > a) v = -0.5 * (sU[tx][a] - sL[a][tx]);   // below the diagonal
-        else v = 0.5 * (sU[a][tx] - sL[tx][a]);
-        Gw[(long long)(l0 + a) * n + j0 + tx] = v;
-    }
-    if (rem != 0)
+    const auto neg = [](double v) {
+        return __hiloint2double(__double2hiint(v) ^ (int)0x80000000, __double2loint(v));
+    };
+    if (rem != 0) {
+        // lower block: G(l0 + l, j0 + j) = -G(j0 + j, l0 + l), stored at Gw[(j0 + j) * n + l0 + l]
         for (int q = 0; q < 4; ++q) {
             const int a = ty + 8 * q;   // j within the tile, tx = l
-            const double v = 0.5 * (sU[tx][a] - sL[a][tx]);
-            Gw[(long long)(j0 + a) * n + l0 + tx] = __hiloint2double(__double2hiint(v) ^ (int)0x80000000,
-                                                                      __double2loint(v));
+            Gw[(long long)(j0 + a) * n + l0 + tx] = neg(sU[tx][a]);
         }
+    } else {
+        // diagonal tile: entries below the diagonal from the ones above it
+        for (int q = 0; q < 4; ++q) {
+            const int a = ty + 8 * q;   // column l = j0 + a, row j = j0 + tx
+            if (tx > a) Gw[(long long)(j0 + a) * n + j0 + tx] = neg(sU[tx][a]);
+            else if (tx == a) Gw[(long long)(j0 + a) * n + j0 + tx] = 0.0;
+        }
+    }
 }
 
 void launch_skew_project(int W, int n, double* G, const uint8_t* go, cudaStream_t st) {

@@ -205,7 +205,8 @@ def test_pf_1024_walkers_n256(case):
 def test_pf_two_particle_moves_1024_walkers_n256(delay):
     """C3's walkers and pairing matrix with two particles moved at once per
     step (Sec. 3.2, 2 rows and 2 columns; B n x 4, C = -J), plain and
-    delayed (K = 8: 32 slot columns), sampled walkers against the oracle."""
+    delayed (K = 8: 32 slot columns), a from-scratch refresh every 32 steps,
+    sampled walkers against the oracle (same refresh schedule)."""
     L = lrugb()
     W, n, m, steps = 1024, 256, 512, 96
     seed = 3
@@ -219,12 +220,15 @@ def test_pf_two_particle_moves_1024_walkers_n256(delay):
     sample = [0, 700, W - 1]
     ratios = np.zeros((steps, len(sample)))
     slot_d, new_d = tdev(slot), tdev(new)
+    every = 32
     for s in range(steps):
         B, idx = st.form_pf_moves(F_d, pos_d, slot_d[s], new_d[s])
         r, _ = st.propose_pf(L.Operand(dense=B, idx=idx, onehot_mask=0b1100))
         st.accept()
         st.commit_moves(pos_d, slot_d[s], new_d[s])
         ratios[s] = r[sample].cpu().numpy()
+        if (s + 1) % every == 0 and s + 1 < steps:
+            st.refresh(st.gather_pairs(F_d, pos_d), want_drift=False)
     inv = st.inverse()[sample].cpu().numpy()
     st.check_device_error()
     for q_, w in enumerate(sample):
@@ -242,7 +246,12 @@ def test_pf_two_particle_moves_1024_walkers_n256(delay):
                 r, Ainv = O.pf_lru(Ainv, B, C, return_update=True)
                 chain.append(r)
             pos[p], pos[q] = sp, sq
-        check_ratios(ratios[:, q_], chain, exact, what=("two-particle", delay, w), ceiling=CEIL_CHAIN)
+            if (s + 1) % every == 0 and s + 1 < steps:
+                A = O.pairing_matrix(F, pos)
+                car = O.init_pf_carrier(A, delay) if delay else None
+                Ainv = O.skew_part(O.inv(A))
+        check_ratios(ratios[:, q_], chain, exact, what=("two-particle", delay, w), refresh_every=every,
+                     ceiling=CEIL_CHAIN)
         assert fro_rel(inv[q_], np.linalg.inv(O.pairing_matrix(F, pos))) <= 1e-9
 
 
