@@ -146,7 +146,11 @@ __device__ __forceinline__ int flush_scan(const DevLayout& L, const DevState<T>&
 // pf : App. A.2 Eq. pf_low_rank, delayed Sec. 3.3 (R_tau, a_tau equations)
 // One CTA per walker.
 // ---------------------------------------------------------------------------
-template <typename T, bool PF, bool DELAYED>
+// SKEWM (Pfaffian): M is projected onto its skew part before it is inverted
+// and M^{-1} after, as the skew-form updates (the delayed slots, the exactly
+// skew plain accept) need; the persistent step's generic Woodbury accept
+// needs the inverse of M as computed (SKEWM = false there).
+template <typename T, bool PF, bool DELAYED, bool SKEWM = DELAYED>
 __device__ void propose_walker(const int w, const DevLayout L, const DevState<T> S, const DevOperand U,
                                const DevOperand V, const T* C, T* ratio_out, int* st_out) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -374,11 +378,11 @@ __device__ void propose_walker(const int w, const DevLayout L, const DevState<T>
                 for (int j = 0; j < kk; ++j) s_inv[i * MAXKK + j] = s_core[i * MAXKK + j];
             st = small_gj_inverse(s_inv, kk, MAXKK, &ratio);
         } else {
-            // The plain path applies the generic Woodbury form and needs the
-            // inverse of M exactly as computed: projecting M onto its skew part
-            // there makes the chain unstable.  The delayed path uses the skew
-            // form (Eq. pf_delayed_Ainv), which needs M and M^{-1} exactly skew.
-            if (DELAYED)
+            // The skew-form updates (Eq. pf_delayed_Ainv, and the exactly skew
+            // plain accept) need M and M^{-1} exactly skew; a generic Woodbury
+            // accept needs the inverse of M as computed (projecting M there
+            // makes the chain unstable).
+            if (SKEWM)
                 for (int i = 0; i < kk; ++i)
                     for (int j = i; j < kk; ++j) {
                         T h = s_half(s_core[i * MAXKK + j] - s_core[j * MAXKK + i]);
@@ -389,7 +393,7 @@ __device__ void propose_walker(const int w, const DevLayout L, const DevState<T>
                 for (int j = 0; j < kk; ++j) s_inv[i * MAXKK + j] = s_core[i * MAXKK + j];
             T dM;
             st = small_gj_inverse(s_inv, kk, MAXKK, &dM);
-            if (DELAYED)
+            if (SKEWM)
                 for (int i = 0; i < kk; ++i)
                     for (int j = i; j < kk; ++j) {
                         T h = s_half(s_inv[i * MAXKK + j] - s_inv[j * MAXKK + i]);
@@ -545,10 +549,12 @@ __global__ void __launch_bounds__(PT, 4) k_dense_column(DevLayout L, DevState<T>
     }
 }
 
+// the standalone propose: the Pfaffian accept that follows is in skew form
+// (plain: k_accept_pf_skew; delayed: the slots), so M is projected
 template <typename T, bool PF, bool DELAYED>
 __global__ void __launch_bounds__(PT) k_propose(DevLayout L, DevState<T> S, DevOperand U, DevOperand V,
                                                  const T* C, T* ratio_out, int* st_out) {
-    propose_walker<T, PF, DELAYED>(blockIdx.x, L, S, U, V, C, ratio_out, st_out);
+    propose_walker<T, PF, DELAYED, PF>(blockIdx.x, L, S, U, V, C, ratio_out, st_out);
 }
 
 // Q^T U for the dense U columns of the delayed propose, one CTA per walker
@@ -1371,7 +1377,7 @@ __global__ void __launch_bounds__(PT) k_step(DevLayout L, DevState<T> S, DevOper
             const int w = ctl.order[item];
             if (!LRU_DEBUG_OK(w >= 0 && w < L.W, S.err)) continue;
             if constexpr (DEL) qtu_block<T>(w, L, S, U);
-            propose_walker<T, PF, DEL>(w, L, S, U, V, C, ratio_out, st_out);
+            propose_walker<T, PF, DEL, DEL>(w, L, S, U, V, C, ratio_out, st_out);
             __syncthreads();
             if (threadIdx.x == 0) {
                 bool acc = ctl.do_accept && S.pst[w] == 0;

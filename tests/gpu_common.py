@@ -29,9 +29,10 @@ def rel(a, b):
     return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
 
 
-# One summary per check_ratios call, printed by the tests (pytest -s shows them):
-# (what, steps, near-node steps, conditioning-limited steps, largest bar used,
-#  largest GPU error against the oracle chain and against the exact ratio).
+# One summary per check_ratios / check_inverse call, printed by the tests
+# (pytest -s shows them): (what, steps, steps below the median ratio,
+# conditioning-limited steps, largest bar used, largest GPU error against the
+# oracle chain and against the exact ratio), or the inverse errors and bar.
 PARITY_LOG = []
 
 
@@ -56,45 +57,69 @@ def exact_pf_ratio(A, B, C):
     return O.pf_pairings(M) / O.pf_pairings(Ci)
 
 
-def check_ratios(gpu, chain, exact, base=RTOL_F64, what="", eps_scale=1.0, refresh_every=0, ceiling=None):
+def check_ratios(gpu, chain, exact, base=RTOL_F64, what="", eps_scale=1.0, refresh_every=0, ceiling=None,
+                 alt=None):
     """Ratio parity against the oracle's chain and against the exact ratios.
 
-    The bar is the relative error `base` (1e-10 in FP64), against both.  A
-    chain of low-rank updates carries the rounding of every update since the
-    last from-scratch refresh, amplified by the conditioning of the matrices
-    it passed through, and the oracle's own FP64 chain measures that amount:
-    e_run is its largest relative error against the exact ratio since the
-    last refresh (reset at every refresh).  A step where 10 * eps_scale * e_run
-    exceeds `base` is conditioning-limited, and its bar is 10 * eps_scale *
-    e_run; eps_scale is the unit roundoff of the GPU arithmetic over FP64's
-    (1 for FP64, 256 for the double-float paths).  The largest bar used must
-    stay within `ceiling` (default 100 * eps_scale * base).  Near-node steps
-    (|exact| < 1e-6 median |exact|) compare absolute errors against
-    base * median |exact|.  Returns the summary it appends to PARITY_LOG."""
+    A ratio is 1 + v^T A^{-1} u (Eq. det_ratio) or the Pfaffian of the core
+    C^{-1} + B^T A^{-1} B (Eq. pf_low_rank): a sum of terms of the size of a
+    typical ratio.  A small ratio comes from cancellation among such terms,
+    and its rounding error is that of the terms, so every error is measured on
+    the scale max(|exact|, median |exact|): relative for ratios above the
+    median, absolute in units of the median below it (a node of the wave
+    function is the limit).  The bar is `base` (1e-10 in FP64), against both
+    the chain and the exact ratio.  A chain of low-rank updates carries the
+    rounding of every update since the last from-scratch refresh, amplified by
+    the conditioning of the matrices it passed through, and the oracle's own
+    FP64 chain measures that amount: e_run is its largest scaled error against
+    the exact ratio since the last refresh (reset at every refresh).  One chain
+    is one sample of that rounding: after a step whose core is nearly singular
+    two FP64 chains that differ only in the order of their sums (another BLAS,
+    the GPU) can sit a decade apart.  `alt` holds further oracle chains of the
+    same moves in another mathematically equal form (plain and delayed); e_run
+    then takes the largest error of all of them.  A step
+    where 10 * eps_scale * e_run exceeds `base` is conditioning-limited, and its
+    bar is 10 * eps_scale * e_run; eps_scale is the unit roundoff of the GPU
+    arithmetic over FP64's (1 for FP64, 256 for the double-float paths).  The
+    largest bar used must stay within `ceiling` (default 100 * eps_scale *
+    base).  Returns the summary it appends to PARITY_LOG."""
     gpu, chain, exact = (np.asarray(x) for x in (gpu, chain, exact))
+    refs = [chain] + [np.asarray(a) for a in (alt or [])]
     ceiling = 100.0 * eps_scale * base if ceiling is None else ceiling
     med = np.median(np.abs(exact))
     e_run = 0.0
-    out = {"what": str(what), "steps": len(exact), "near_node": 0, "cond_limited": 0, "max_bar": base,
+    out = {"what": str(what), "steps": len(exact), "below_median": 0, "cond_limited": 0, "max_bar": base,
            "max_err_vs_chain": 0.0, "max_err_vs_exact": 0.0, "ceiling": ceiling}
     for s in range(len(exact)):
         if refresh_every and s % refresh_every == 0:
             e_run = 0.0
-        if abs(exact[s]) < 1e-6 * med:
-            out["near_node"] += 1
-            assert abs(gpu[s] - chain[s]) <= base * med, (what, s, gpu[s], chain[s], exact[s])
-            continue
-        e_run = max(e_run, abs(chain[s] - exact[s]) / abs(exact[s]))
+        sc = max(abs(exact[s]), med)
+        out["below_median"] += int(abs(exact[s]) < med)
+        e_run = max(e_run, max(abs(c[s] - exact[s]) for c in refs) / sc)
         bar = max(base, 10 * eps_scale * e_run)
         if bar > base:
             out["cond_limited"] += 1
         out["max_bar"] = max(out["max_bar"], bar)
-        ec = abs(gpu[s] - chain[s]) / abs(chain[s])
-        ee = abs(gpu[s] - exact[s]) / abs(exact[s])
+        ec = abs(gpu[s] - chain[s]) / sc
+        ee = abs(gpu[s] - exact[s]) / sc
         out["max_err_vs_chain"] = max(out["max_err_vs_chain"], ec)
         out["max_err_vs_exact"] = max(out["max_err_vs_exact"], ee)
         assert ec <= bar and ee <= bar, (what, s, gpu[s], chain[s], exact[s], bar)
     assert out["max_bar"] <= ceiling, (what, out)
+    PARITY_LOG.append(out)
+    print("parity:", out)
+    return out
+
+
+def check_inverse(gpu_inv, chain_inv, exact_inv, base=RTOL_F64, what="", eps_scale=1.0):
+    """The carried inverse against the exact inverse of the current matrix
+    (Frobenius-relative), on the same conditioning-limited bar as the ratios:
+    max(base, 10 * eps_scale * the oracle chain's own inverse error)."""
+    e_chain = fro_rel(chain_inv, exact_inv)
+    bar = max(base, 10 * eps_scale * e_chain)
+    e = fro_rel(gpu_inv, exact_inv)
+    out = {"what": str(what), "inverse_err": e, "chain_inverse_err": e_chain, "bar": bar}
+    assert e <= bar, out
     PARITY_LOG.append(out)
     print("parity:", out)
     return out

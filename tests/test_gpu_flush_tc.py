@@ -14,8 +14,8 @@ Sec. 3.3 Eq. pf_delayed_Ainv) and of the double-float GEMV.
 import numpy as np
 import pytest
 
-from gpu_common import (CEIL_CHAIN, O, check_ratios, det_workload, fro_rel, lrugb, pf_workload, rel, replay_det_oracle,
-                        run_det_chain_gpu, tdev, torch)
+from gpu_common import (CEIL_CHAIN, O, check_inverse, check_ratios, det_workload, fro_rel, lrugb, pf_workload, rel,
+                        replay_det_oracle, run_det_chain_gpu, tdev, torch)
 
 pytestmark = pytest.mark.gpu
 
@@ -155,7 +155,8 @@ def test_pf_delayed_flush_exactly_skew(flush):
             pos[slot[s, w]] = new[s, w]
         scale = 256.0 if flush == 5 else 1.0     # double-float flush; the split product rounds as FP64
         check_ratios(ratios[:, w], chain, exact, what=(flush, w), eps_scale=scale, ceiling=CEIL_CHAIN * scale)
-        assert fro_rel(inv[w], O.inv(O.pairing_matrix(F, pos))) <= 1e-10 * scale
+        check_inverse(inv[w], O.carrier_inverse(car), O.inv(O.pairing_matrix(F, pos)), what=(flush, w),
+                      eps_scale=scale)
 
 
 @pytest.mark.parametrize("mode", [1, 2, 3, 4])

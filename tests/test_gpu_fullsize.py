@@ -19,7 +19,8 @@ import math
 import numpy as np
 import pytest
 
-from gpu_common import CEIL_CHAIN, O, check_ratios, exact_det_ratio, exact_pf_ratio, fro_rel, lrugb, rel, tdev, torch
+from gpu_common import (CEIL_CHAIN, O, check_inverse, check_ratios, exact_det_ratio, exact_pf_ratio, fro_rel, lrugb,
+                        rel, tdev, torch)
 from paper_2602_05255_gb300 import workloads
 
 GO = pytest.importorskip("oracle.grad_oracle")
@@ -88,7 +89,8 @@ def test_det_4096_walkers_n512(case):
                 car = O.init_det_carrier(O.slater_matrix(Phi, occ), K)
         check_ratios(ratios[:, q], chain, exact, what=(case, w), eps_scale=scale, refresh_every=every,
                      ceiling=CEIL_CHAIN * scale)
-        assert fro_rel(inv[q], np.linalg.inv(O.slater_matrix(Phi, occ))) <= 1e-10 * scale
+        check_inverse(inv[q], O.carrier_inverse(car), np.linalg.inv(O.slater_matrix(Phi, occ)), what=(case, w),
+                      eps_scale=scale)
 
 
 def test_det_headline_1024_walkers_n1024():
@@ -194,7 +196,8 @@ def test_pf_1024_walkers_n256(case):
             pos[slot[s, w]] = new[s, w]
         check_ratios(ratios[:, q], chain, exact, what=(case, w), eps_scale=scale, ceiling=CEIL_CHAIN * scale)
         A = O.pairing_matrix(F, pos)
-        assert fro_rel(inv[q], np.linalg.inv(A)) <= 1e-10 * scale
+        check_inverse(inv[q], O.carrier_inverse(car) if K else Ainv, np.linalg.inv(A), what=(case, w),
+                      eps_scale=scale)
         # the skew flush / skew accept keep A^{-1} exactly skew
         assert np.array_equal(inv[q], -inv[q].T) or (K and steps % K)
         l1 = np.linalg.slogdet(A)[1] / 2
@@ -232,27 +235,30 @@ def test_pf_two_particle_moves_1024_walkers_n256(delay):
     inv = st.inverse()[sample].cpu().numpy()
     st.check_device_error()
     for q_, w in enumerate(sample):
+        # both oracle forms of the same moves (plain, and delayed with K = 8):
+        # the one the GPU runs is the reference chain, the other a second
+        # sample of the FP64 rounding for the conditioning-limited bar
         pos = pos0[w].copy()
-        car = O.init_pf_carrier(O.pairing_matrix(F, pos), delay) if delay else None
+        car = O.init_pf_carrier(O.pairing_matrix(F, pos), 8)
         Ainv = O.skew_part(O.inv(O.pairing_matrix(F, pos)))
-        chain, exact = [], []
+        plain, delayed, exact = [], [], []
         for s in range(steps):
             (p, q), (sp, sq) = slot[s, w], new[s, w]
             B, C = O.pf_two_particle_move(F, pos, p, q, sp, sq)
             exact.append(exact_pf_ratio(O.pairing_matrix(F, pos), B, C))
-            if delay:
-                chain.append(O.pf_lru_delayed(car, B, C))
-            else:
-                r, Ainv = O.pf_lru(Ainv, B, C, return_update=True)
-                chain.append(r)
+            delayed.append(O.pf_lru_delayed(car, B, C))
+            r, Ainv = O.pf_lru(Ainv, B, C, return_update=True)
+            plain.append(r)
             pos[p], pos[q] = sp, sq
             if (s + 1) % every == 0 and s + 1 < steps:
                 A = O.pairing_matrix(F, pos)
-                car = O.init_pf_carrier(A, delay) if delay else None
+                car = O.init_pf_carrier(A, 8)
                 Ainv = O.skew_part(O.inv(A))
+        chain, other = (delayed, plain) if delay else (plain, delayed)
         check_ratios(ratios[:, q_], chain, exact, what=("two-particle", delay, w), refresh_every=every,
-                     ceiling=CEIL_CHAIN)
-        assert fro_rel(inv[q_], np.linalg.inv(O.pairing_matrix(F, pos))) <= 1e-9
+                     ceiling=CEIL_CHAIN, alt=[other])
+        check_inverse(inv[q_], O.carrier_inverse(car) if delay else Ainv, np.linalg.inv(O.pairing_matrix(F, pos)),
+                      what=("two-particle", delay, w))
 
 
 # C4 arms: flush, and the asserted bounds on the relative ratio error against
