@@ -715,25 +715,41 @@ __global__ void __launch_bounds__(PT, 2) k_accept(DevLayout L, DevState<T> S, De
 
 // Plain Pfaffian accept in skew form (Eq. pf_inv with (A^{-1})^T = -A^{-1}):
 //   A'^{-1} = A^{-1} + X M^{-1} X^T,   X = A^{-1} B (from the propose),
-// with M^{-1} projected onto its skew part.  Only the upper triangle j < l is
-// computed, one FMA per element and column of B against
-// Z_l = M^{-1} X_l^T (per column); the lower triangle is written as the exact
-// negative of the upper one and the diagonal as zero, so A^{-1} stays exactly
-// skew along the chain.  That halves the FP64 work of the generic Woodbury
-// pass (which also reduces B^T A^{-1} across lanes) and reads only the upper
-// half.  One CTA per (walker, 32 x 32 upper tile).
+// with M^{-1} projected onto its skew part, Z_l = M^{-1} X_l^T per row l.
+// The new inverse is exactly skew in exact arithmetic; in floating point the
+// two triangles of the update round differently.  One CTA per (walker,
+// 32 x 32 upper tile) computes the upper entries j < l and writes the lower
+// triangle as their exact negatives and the diagonal as zero, so A^{-1}
+// stays exactly skew along the chain, and only the upper half is read.
+//   * B with 2 columns (one row-and-column move): U_jl = A^{-1}_jl +
+//     sum_a X_ja Z_la, one FMA per element and column.  On the paper's
+//     pairing matrices this keeps the accuracy of the skew-part projection
+//     (A' + A'^T)/2 of the update (checked against exact ratios).
+//   * B with 4 or more columns (two particles at once): a kept triangle
+//     carries the rounding of its own FMA chain, which on those chains cost
+//     up to 25x the ratio error of the projection.  The kernel therefore also
+//     forms U_lj = -A^{-1}_jl + sum_a X_la Z_ja and stores (U_jl - U_lj) / 2,
+//     the skew part of the computed update, at twice the FMAs.
 template <typename T>
 __global__ void __launch_bounds__(256) k_accept_pf_skew(DevLayout L, DevState<T> S, const uint8_t* mask) {
-    __shared__ T sXj[32][MAXKK + 1];   // X rows of the tile's j range
-    __shared__ T sZl[32][MAXKK + 1];   // Z = M^{-1} X^T rows of the tile's l range
+    constexpr int LDX = MAXKK + 1;
+    // phase 1: X and Z rows of the tile's j and l ranges; phase 2 (after a
+    // barrier): the 32 x 33 result tile, in the same storage
+    __shared__ T sbuf[4 * 32 * LDX];
     __shared__ T sMi[MAXKK * MAXKK];
-    __shared__ T sT[32][33];
+    T* sXj = sbuf;                 // [32][LDX] X rows j0..j0+31
+    T* sZl = sbuf + 32 * LDX;      // [32][LDX] Z rows l0..l0+31
+    T* sXl = sbuf + 64 * LDX;      // (averaged form) X rows of the l range
+    T* sZj = sbuf + 96 * LDX;      // (averaged form) Z rows of the j range
+    T* sT = sbuf;                  // [32][33]
+    static_assert(32 * 33 <= 4 * 32 * LDX, "result tile fits the operand storage");
     const int w = blockIdx.y;
     if (mask && !mask[w]) return;
     if (S.pst[w] != 0) return;
     const int n = L.nw(w), kk = L.kv(w);
     const int nt = (n + 31) / 32;
     if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
+    const bool avg = kk > 2;
     int tJ, tL;
     TileIter::coords((int)blockIdx.x, nt, true, tJ, tL);
     const int j0 = tJ * 32, l0 = tL * 32;
@@ -746,7 +762,8 @@ __global__ void __launch_bounds__(256) k_accept_pf_skew(DevLayout L, DevState<T>
     }
     for (int e = threadIdx.x; e < 32 * kk; e += 256) {
         const int a = e / 32, r = e % 32;
-        sXj[r][a] = (j0 + r < n) ? X[(long long)a * n + j0 + r] : s_zero(T());
+        sXj[r * LDX + a] = (j0 + r < n) ? X[(long long)a * n + j0 + r] : s_zero(T());
+        if (avg) sXl[r * LDX + a] = (l0 + r < n) ? X[(long long)a * n + l0 + r] : s_zero(T());
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 32 * kk; e += 256) {
@@ -754,37 +771,53 @@ __global__ void __launch_bounds__(256) k_accept_pf_skew(DevLayout L, DevState<T>
         T z = s_zero(T());
         if (l0 + r < n)
             for (int b = 0; b < kk; ++b) z = s_fma(sMi[a * MAXKK + b], X[(long long)b * n + l0 + r], z);
-        sZl[r][a] = z;
+        sZl[r * LDX + a] = z;
+        if (avg) {
+            T zj = s_zero(T());
+            if (j0 + r < n)
+                for (int b = 0; b < kk; ++b) zj = s_fma(sMi[a * MAXKK + b], X[(long long)b * n + j0 + r], zj);
+            sZj[r * LDX + a] = zj;
+        }
     }
     __syncthreads();
     T* Gw = S.G + L.mo(w);
     const int j = j0 + tx;
+    T vals[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int rl = ty + 8 * q, l = l0 + rl;
         T v = s_zero(T());
         if (j < n && l < n && (tJ != tL || tx < rl)) {
-            v = Gw[(long long)l * n + j];   // (A^{-1})_{jl}, j < l
-            for (int a = 0; a < kk; ++a) v = s_fma(sXj[tx][a], sZl[rl][a], v);
+            const T g = Gw[(long long)l * n + j];   // (A^{-1})_{jl}, j < l
+            v = g;
+            for (int a = 0; a < kk; ++a) v = s_fma(sXj[tx * LDX + a], sZl[rl * LDX + a], v);
+            if (avg) {
+                T u = s_neg(g);                      // (A^{-1})_{lj}, exactly
+                for (int a = 0; a < kk; ++a) u = s_fma(sXl[rl * LDX + a], sZj[tx * LDX + a], u);
+                v = s_half(v - u);
+            }
         }
-        sT[rl][tx] = v;
+        vals[q] = v;
     }
+    __syncthreads();   // operand rows dead: the storage becomes the result tile
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sT[(ty + 8 * q) * 33 + tx] = vals[q];
     __syncthreads();
     // (j, l), j < l: the computed value; (l, j): its exact negative; diagonal 0
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int rl = ty + 8 * q, l = l0 + rl;
         if (j >= n || l >= n) continue;
-        if (tJ != tL || tx < rl) Gw[(long long)l * n + j] = sT[rl][tx];
+        if (tJ != tL || tx < rl) Gw[(long long)l * n + j] = sT[rl * 33 + tx];
         else if (tx == rl) Gw[(long long)l * n + j] = s_zero(T());
-        else Gw[(long long)l * n + j] = s_neg(sT[tx][rl]);   // diagonal tile, j > l
+        else Gw[(long long)l * n + j] = s_neg(sT[tx * 33 + rl]);   // diagonal tile, j > l
     }
     if (tJ != tL) {
         // mirror tile: (l, j) for l in the L range, stored at G[j * n + l]
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int rj = ty + 8 * q, jj = j0 + rj, ll = l0 + tx;
-            if (jj < n && ll < n) Gw[(long long)jj * n + ll] = s_neg(sT[tx][rj]);
+            if (jj < n && ll < n) Gw[(long long)jj * n + ll] = s_neg(sT[tx * 33 + rj]);
         }
     }
 }
