@@ -66,7 +66,7 @@ PRESETS = {
            "dtype": "f64", "var": None, "first_rows": False, "arms": "plain,delayed,delayed_fp64gemv",
            "main": "delayed"},
     "c3": {"kind": "pf", "walkers": 1024, "n": 256, "m": 512, "k": 1, "delay": 8, "refresh_every": 0,
-           "dtype": "f64", "arms": "plain,delayed,delayed_native,delayed_dfflush", "main": "delayed"},
+           "dtype": "f64", "arms": "plain,delayed,delayed_dfpass,delayed_native,delayed_dfflush", "main": "delayed"},
     "c4": {"kind": "det", "walkers": 64, "n": 2048, "m": 4096, "k": 2, "delay": 32, "refresh_every": 64,
            "dtype": "f64", "var": None, "first_rows": False,
            "arms": "plain,delayed_fp64gemv,delayed_tf32x3,delayed_bf16x3,delayed_tf32,delayed_bf16",
@@ -104,6 +104,7 @@ PF_ARMS = {
     "delayed_native": (None, "native", "native"),   # FP64 skew flush
     "delayed_dfflush": (None, "native", "df"),      # double-float skew flush
     "delayed_df": (None, "df", "df"),               # double-float pass and flush
+    "delayed_dfpass": (None, "df", "split"),        # double-float pass, split-product flush
     "plain_dfprop": (0, "df", "native"),
 }
 

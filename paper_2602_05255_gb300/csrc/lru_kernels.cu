@@ -1198,7 +1198,8 @@ __global__ void k_commit(DevLayout L, DevState<T> S, const uint8_t* mask, bool d
 // native flush: A_0^{-1} -= P Q^T (det, Eq. delayed_Ainv) or += (pf, Eq.
 // pf_delayed_Ainv) over the filled slots.  32 x 32 tiles; for the Pfaffian only
 // tiles with J <= L are computed and the mirror is written as the exact
-// negative transpose, so A_0^{-1} stays exactly skew.
+// negative transpose, so A_0^{-1} stays exactly skew (for B of 4 or more
+// columns the kept value is the skew part of the update, see below).
 // ---------------------------------------------------------------------------
 template <typename T, bool PF, int CH = 64>
 __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int w, int tau, int tJ, int tL,
@@ -1212,24 +1213,40 @@ __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int 
     T* Gw = S.G + L.mo(w);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     const int j0 = tJ * 32, l0 = tL * 32;
-    T acc[4];
+    // Pfaffian with B of 4 or more columns (two-particle moves): the update
+    // P Q^T is skew in exact arithmetic, and a kept triangle would carry the
+    // rounding of its own FMA chain; the tile then also forms (P Q^T)_lj in a
+    // second pass over the slots and adds the skew part (D_jl - D_lj) / 2, as
+    // the plain skew accept does (one-particle moves measure the same either way).
+    const bool avg = PF && kk > 2;
+    T acc[4], acc2[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = s_zero(T());
-    for (int c0 = 0; c0 < cu; c0 += CH) {
-        for (int e = threadIdx.x; e < 32 * CH; e += 256) {
-            const int r = e / CH, c = e % CH;
-            const bool okc = c0 + c < cu;
-            sP[r * LD + c] = (okc && j0 + r < n) ? S.P[(vo + j0 + r) * Kc + c0 + c] : s_zero(T());
-            sQ[r * LD + c] = (okc && l0 + r < n) ? S.Q[(vo + l0 + r) * Kc + c0 + c] : s_zero(T());
-        }
-        __syncthreads();
-        const int cm = min(CH, cu - c0);
-        for (int c = 0; c < cm; ++c) {
-            T pj = sP[tx * LD + c];
+    for (int q = 0; q < 4; ++q) acc[q] = acc2[q] = s_zero(T());
+    for (int pass = 0; pass < (avg ? 2 : 1); ++pass) {
+        // pass 0: P rows of the j range against Q rows of the l range; pass 1: swapped
+        const T* Pa = pass ? S.Q : S.P;
+        const T* Qa = pass ? S.P : S.Q;
+        for (int c0 = 0; c0 < cu; c0 += CH) {
+            for (int e = threadIdx.x; e < 32 * CH; e += 256) {
+                const int r = e / CH, c = e % CH;
+                const bool okc = c0 + c < cu;
+                sP[r * LD + c] = (okc && j0 + r < n) ? Pa[(vo + j0 + r) * Kc + c0 + c] : s_zero(T());
+                sQ[r * LD + c] = (okc && l0 + r < n) ? Qa[(vo + l0 + r) * Kc + c0 + c] : s_zero(T());
+            }
+            __syncthreads();
+            const int cm = min(CH, cu - c0);
+            for (int c = 0; c < cm; ++c) {
+                T pj = sP[tx * LD + c];
+                if (pass == 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = s_fma(pj, sQ[(ty + 8 * q) * LD + c], acc[q]);
+                    for (int q = 0; q < 4; ++q) acc[q] = s_fma(pj, sQ[(ty + 8 * q) * LD + c], acc[q]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc2[q] = s_fma(pj, sQ[(ty + 8 * q) * LD + c], acc2[q]);
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
     // element (j0+tx, l0+ty+8q) lives at G[(l0+ty+8q)*n + j0+tx]
 #pragma unroll
@@ -1238,7 +1255,9 @@ __device__ void flush_native_tile(const DevLayout& L, const DevState<T>& S, int 
         T nv = s_zero(T());
         if (j < n && l < n) {
             T g = Gw[(long long)l * n + j];
-            nv = PF ? (g + acc[q]) : (g - acc[q]);
+            // acc2[q] = (Q P^T)_jl = (P Q^T)_lj
+            const T d = avg ? s_half(acc[q] - acc2[q]) : acc[q];
+            nv = PF ? (g + d) : (g - d);
         }
         sT[(ty + 8 * q) * 33 + tx] = nv;
     }
