@@ -66,7 +66,7 @@ PRESETS = {
            "dtype": "f64", "var": None, "first_rows": False, "arms": "plain,delayed,delayed_fp64gemv",
            "main": "delayed"},
     "c3": {"kind": "pf", "walkers": 1024, "n": 256, "m": 512, "k": 1, "delay": 8, "refresh_every": 0,
-           "dtype": "f64", "arms": "plain,delayed,delayed_dfpass,delayed_native,delayed_dfflush", "main": "delayed"},
+           "dtype": "f64", "arms": "plain,plain_dfprop,delayed_dfpass,delayed,delayed_native,delayed_dfflush", "main": "delayed_dfpass"},
     "c4": {"kind": "det", "walkers": 64, "n": 2048, "m": 4096, "k": 2, "delay": 32, "refresh_every": 64,
            "dtype": "f64", "var": None, "first_rows": False,
            "arms": "plain,delayed_fp64gemv,delayed_tf32x3,delayed_bf16x3,delayed_tf32,delayed_bf16",
@@ -1283,7 +1283,7 @@ def main():
         if args.config == "headline" and not args.no_pf:
             # the Pfaffian workload (c3) in the same run, at the same steps
             pcfg = dict(PRESETS["c3"])
-            pcfg["arms"] = "plain,delayed,delayed_dfflush"
+            pcfg["arms"] = "plain,delayed_dfpass,delayed"
             pargs = argparse.Namespace(**vars(args))
             pargs.no_e2e, pargs.no_cpu_baseline = True, True
             pl = main_pf(pargs, pcfg, torch, L, rank, world, dist)

@@ -145,6 +145,12 @@ void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mas
 void launch_oz_panel(int W, int w0, int n, int k0, const OzWork& Z, const uint8_t* mask, cudaStream_t st);
 // one 16-column sub-panel (n <= 1024): elimination and its row exchanges on the
 // other panel columns; the last one of a panel also exchanges the outside columns
+// the tensor-core refresh eliminates its panels in FP64 sub-panels (pivots
+// recorded per row, log|det| summed at the end) up to this n
+constexpr int OZ_SUBPANEL_MAX_N = 2048;
+// width of the FP64 sub-panels of the tensor-core refresh for this n (16, or 8
+// above n = 1024, where a thread holds four rows)
+int oz_subpanel_width(int n);
 bool launch_oz_subpanel(int W, int n, int k0, int sp, const OzWork& Z, const uint8_t* mask, cudaStream_t st);
 void launch_oz_finish(int W, int n, const OzWork& Z, const DevState<double>& S, const uint8_t* mask, bool delayed,
                       bool reset_tau, cudaStream_t st);

@@ -549,6 +549,85 @@ __global__ void __launch_bounds__(PT, 4) k_dense_column(DevLayout L, DevState<T>
     }
 }
 
+// columns (rows) per CTA of the warp-per-column (row) double-float passes
+constexpr int DF_CPB = 64;
+
+// The same pass for an exactly skew A^{-1} (every Pfaffian state: the skew
+// accept, the skew flushes and the refresh keep it so), in double-float
+// arithmetic: X_j = sum_l (A^{-1})_{jl} u_l = -sum_l (A^{-1})_{lj} u_l, and
+// (A^{-1})_{lj} lies at G[j n + l], so row j of the sum is contiguous in
+// memory.  One WARP per row j reads it in 16-byte loads (512 contiguous bytes
+// per load instruction), with a batch of loads in flight while the previous
+// one is multiplied, as in k_accept_delayed_warp_df; the products run on the
+// FP32 and integer pipes, so the pass is bound by HBM rather than by the FP64
+// pipe.  One CTA (8 warps) per walker and DF_CPB rows.  n even.
+template <int NP2>
+__global__ void __launch_bounds__(PT, 2) k_dense_column_skew_df(DevLayout L, DevState<double> S, DevOperand U,
+                                                                 int a) {
+    constexpr int BS = NP2 == 16 ? 4 : (NP2 > 16 ? 8 : NP2 / 2);   // 16-byte loads per lane per batch
+    constexpr int NBT = NP2 / BS;                 // batches per row (even)
+    __shared__ __align__(16) float4 sU4[32 * NP2];   // (hi u_2p, hi u_2p+1, lo u_2p, lo u_2p+1)
+    const int w = blockIdx.x;
+    const int n = L.nw(w);
+    const int np = n >> 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int j0 = blockIdx.y * DF_CPB;
+    if (j0 >= n) return;
+    if (!LRU_DEBUG_OK((n & 1) == 0 && np <= 32 * NP2, S.err)) return;
+    const int nrow = min(n - j0, DF_CPB);
+    const double* ub = vec_ptr<double>(U, L, w, a, n);
+    for (int p = threadIdx.x; p < 32 * NP2; p += PT) {
+        const double u0 = p < np ? ub[2 * p] : 0.0, u1 = p < np ? ub[2 * p + 1] : 0.0;
+        float h0, lo0, h1, lo1;
+        split_d(u0, h0, lo0);
+        split_d(u1, h1, lo1);
+        sU4[p] = make_float4(h0, h1, lo0, lo1);
+    }
+    __syncthreads();
+    const double* Gw = S.G + L.mo(w);
+    double* Xa = S.X + L.vo(w) * L.kk + (long long)a * n;
+    // this warp's rows j0 + wid + 8 i, as a flat sequence of (row, batch) items
+    const int nmine = nrow > wid ? (nrow - wid + 7) / 8 : 0;
+    const int T = nmine * NBT;
+    auto load = [&](double2 (&buf)[BS], int t) {
+        const int c = t / NBT, b = t % NBT;
+        const double2* r2 = reinterpret_cast<const double2*>(Gw + (long long)(j0 + wid + 8 * c) * n);
+#pragma unroll
+        for (int m = 0; m < BS; ++m) {
+            const int p = lane + 32 * (b * BS + m);
+            buf[m] = p < np ? r2[p] : make_double2(0.0, 0.0);
+        }
+    };
+    float ah0 = 0.f, al0 = 0.f, ah1 = 0.f, al1 = 0.f;
+    auto compute = [&](const double2 (&buf)[BS], int t) {
+        const int b = t % NBT;
+#pragma unroll
+        for (int m = 0; m < BS; ++m) {
+            const int p = lane + 32 * (b * BS + m);
+            float gh, gl;
+            const float4 v = sU4[p];
+            split_d(buf[m].x, gh, gl);
+            df_fma(ah0, al0, v.x, v.z, gh, gl);
+            split_d(buf[m].y, gh, gl);
+            df_fma(ah1, al1, v.y, v.w, gh, gl);
+        }
+        if (b == NBT - 1) {
+            df_add(ah0, al0, ah1, al1);
+            df_warp_sum(ah0, al0);
+            if (lane == 0) Xa[j0 + wid + 8 * (t / NBT)] = -df_to_double(ah0, al0);
+            ah0 = al0 = ah1 = al1 = 0.f;
+        }
+    };
+    double2 buf0[BS], buf1[BS];
+    if (T > 0) load(buf0, 0);
+    for (int t = 0; t < T; t += 2) {   // T is even
+        load(buf1, t + 1);
+        compute(buf0, t);
+        if (t + 2 < T) load(buf0, t + 2);
+        compute(buf1, t + 1);
+    }
+}
+
 // the standalone propose: the Pfaffian accept that follows is in skew form
 // (plain: k_accept_pf_skew; delayed: the slots), so M is projected
 template <typename T, bool PF, bool DELAYED>
@@ -904,7 +983,6 @@ __global__ void __launch_bounds__(PT, 2) k_accept_delayed_lane(DevLayout L, DevS
 // once per CTA by one thread per column: a warp-wide FP64 instruction
 // occupies the FP64 pipe for many cycles even with one lane active.  One CTA
 // (8 warps) per walker and DF_CPB columns.
-constexpr int DF_CPB = 64;   // columns per CTA of the warp-per-column double-float accept
 
 template <int NP2>
 __global__ void __launch_bounds__(PT, 2) k_accept_delayed_warp_df(DevLayout L, DevState<double> S, DevOperand V,
@@ -1739,7 +1817,19 @@ void launch_propose(bool pf, bool delayed, bool df, const DevLayout& L, const De
         const int nr = (L.n_max + PT - 1) / PT;
         bool launched = false;
         if constexpr (std::is_same<T, double>::value) {
-            if (df) {
+            if (df && pf && L.n_uni > 0 && (L.n_uni % 2) == 0 && L.n_uni <= 2048) {
+                // Pfaffian: A^{-1} is exactly skew, so X = -(u^T A^{-1})^T streams
+                // contiguous rows, one warp each
+                dim3 grid(L.W, (L.n_max + DF_CPB - 1) / DF_CPB);
+                const int np2 = (L.n_max / 2 + 31) / 32;
+#define LRU_PF_WDF(N) \
+    case N: k_dense_column_skew_df<N><<<grid, PT, 0, st>>>(L, S, U, a); break;
+                switch (np2 <= 4 ? 4 : (np2 <= 8 ? 8 : (np2 <= 16 ? 16 : 32))) {
+                    LRU_PF_WDF(4) LRU_PF_WDF(8) LRU_PF_WDF(16) LRU_PF_WDF(32) default: break;
+                }
+#undef LRU_PF_WDF
+                launched = true;
+            } else if (df) {
                 if (nr <= 1) k_dense_column<T, 1, true><<<L.W, PT, 0, st>>>(L, S, U, a);
                 else if (nr <= 2) k_dense_column<T, 2, true><<<L.W, PT, 0, st>>>(L, S, U, a);
                 else if (nr <= 4) k_dense_column<T, 4, true><<<L.W, PT, 0, st>>>(L, S, U, a);

@@ -504,23 +504,22 @@ __global__ void __launch_bounds__(RT) k_oz_panel(int n, int k0, int w0, OzWork Z
     }
 }
 
-// One 16-column sub-panel of panel [k0, k0 + OZ_B) with the rows in registers
-// (n <= 1024): thread t owns rows t + q * blockDim (q < RPT, blockDim = n /
-// RPT).  The sub-panel is eliminated in registers (pivot by a block reduction,
+// One SW-column sub-panel of panel [k0, k0 + OZ_B) with the rows in registers
+// (SW = 16 for n <= 1024, 8 up to n = 2048): thread t owns rows t + q * blockDim
+// (q < RPT, blockDim = n / RPT).  The sub-panel is eliminated in registers (pivot by a block reduction,
 // row swaps through shared memory) and its transform columns written back;
 // its row exchanges are then applied to the other panel columns, whose update
 // by the transform is a split product on the tensor cores (refresh_oz.cu).
 // The last sub-panel of a panel also applies the panel's exchanges, in pivot
 // order, to the columns outside it.  Pivots go to Z.piv (log|det| and the
 // sign are summed at the end).
-template <int RPT>
+template <int RPT, int SW>
 __global__ void __launch_bounds__(512, 1) k_oz_subpanel_rows(int n, int k0, int sp, OzWork Z, const uint8_t* mask) {
-    constexpr int SW = 16;                   // sub-panel width
+    static_assert(SW % 2 == 0 && OZ_B % SW == 0, "sub-panel width");
     __shared__ double s_rowk[SW], s_bufA[SW], s_bufB[SW];
-    __shared__ double s_wv[16];
+    __shared__ unsigned long long s_wk[16];
     __shared__ int s_wi[16];
-    __shared__ double s_bv;
-    __shared__ int s_bi, s_sing;
+    __shared__ int s_sing;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
     const int w = blockIdx.x;
     if (mask && !mask[w]) return;
@@ -545,83 +544,72 @@ __global__ void __launch_bounds__(512, 1) k_oz_subpanel_rows(int n, int k0, int 
         for (int kc = 0; kc < SW; ++kc) {
             const int k = ks + kc;
             // ---- pivot: largest |v| over rows >= k (ties: smallest row) ----
-            double bv = -1.0;
+            // |v| is compared through its bit pattern (a non-negative double
+            // orders like its bits as an unsigned integer), so the search runs on
+            // the integer pipe and leaves the FP64 pipe to the elimination; NaN
+            // counts as 0.  Every warp then reduces the per-warp winners itself,
+            // so the pivot costs one barrier.
+            unsigned long long bk = 0ull;
             int bi = -1;
 #pragma unroll
             for (int q = 0; q < RPT; ++q) {
                 const int r = tid + q * nt;
-                const double a = fabs(v[q][kc]);
-                if (r >= k && a > bv) { bv = a; bi = r; }
+                unsigned long long a = (unsigned long long)__double_as_longlong(v[q][kc]) & 0x7FFFFFFFFFFFFFFFull;
+                if (a > 0x7FF0000000000000ull) a = 0ull;
+                if (r >= k && (bi < 0 || a > bk)) { bk = a; bi = r; }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) { bv = ov; bi = oi; }
+                if (oi >= 0 && (bi < 0 || ok > bk || (ok == bk && oi < bi))) { bk = ok; bi = oi; }
             }
-            if (lane == 0) { s_wv[wid] = bv; s_wi[wid] = bi; }
+            if (lane == 0) { s_wk[wid] = bk; s_wi[wid] = bi; }
             __syncthreads();
-            if (wid == 0) {
-                bv = lane < nt / 32 ? s_wv[lane] : -1.0;
-                bi = lane < nt / 32 ? s_wi[lane] : -1;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                    if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) { bv = ov; bi = oi; }
-                }
-                if (lane == 0) { s_bv = bv; s_bi = bi; }
+            bk = 0ull;
+            bi = -1;
+            for (int q = 0; q < nt / 32; ++q) {
+                const unsigned long long ok = s_wk[q];
+                const int oi = s_wi[q];
+                if (oi >= 0 && (bi < 0 || ok > bk || (ok == bk && oi < bi))) { bk = ok; bi = oi; }
             }
-            __syncthreads();
-            const int p = s_bi;
-            if (!(s_bv > 0.0) || p < 0) {
+            const int p = bi;
+            if (bk == 0ull || p < 0) {
                 if (tid == 0) { perm[k] = k; s_sing = 1; Z.piv[(long long)w * n + k] = 0.0; }
+                __syncthreads();   // every thread has read s_wk before the next pivot writes it
                 continue;
             }
             if (tid == 0) perm[k] = p;
             const int tk = k % nt, qk = k / nt, tp = p % nt, qp = p / nt;
-            // ---- exchange rows k and p (sub-panel part) ----
-            if (p != k) {
+            // ---- rows p (the pivot row) and k to shared memory ----
 #pragma unroll
-                for (int q = 0; q < RPT; ++q) {
-                    if (tid == tk && q == qk)
-#pragma unroll
-                        for (int c = 0; c < SW; ++c) s_bufA[c] = v[q][c];
-                    if (tid == tp && q == qp)
-#pragma unroll
-                        for (int c = 0; c < SW; ++c) s_bufB[c] = v[q][c];
-                }
-                __syncthreads();
-#pragma unroll
-                for (int q = 0; q < RPT; ++q) {
-                    if (tid == tk && q == qk)
-#pragma unroll
-                        for (int c = 0; c < SW; ++c) v[q][c] = s_bufB[c];
-                    if (tid == tp && q == qp)
-#pragma unroll
-                        for (int c = 0; c < SW; ++c) v[q][c] = s_bufA[c];
-                }
-                __syncthreads();   // s_bufA is reused just below
-            }
-            // ---- scale the pivot row: 16 threads, one element each; the pivot
-            //      is recorded (log|det| and the sign are summed at the end) ----
-#pragma unroll
-            for (int q = 0; q < RPT; ++q)
-                if (tid == tk && q == qk)
+            for (int q = 0; q < RPT; ++q) {
+                if (tid == tp && q == qp)
 #pragma unroll
                     for (int c = 0; c < SW; ++c) s_bufA[c] = v[q][c];
+                if (p != k && tid == tk && q == qk)
+#pragma unroll
+                    for (int c = 0; c < SW; ++c) s_bufB[c] = v[q][c];
+            }
             __syncthreads();
+            // ---- scale the pivot row: 16 threads, one element each; the pivot
+            //      is recorded (log|det| and the sign are summed at the end) ----
             if (tid < SW) {
                 const double piv = s_bufA[kc];
                 s_rowk[tid] = (tid == kc ? 1.0 : s_bufA[tid]) / piv;
                 if (tid == 0) Z.piv[(long long)w * n + k] = piv;
             }
             __syncthreads();
+            // ---- exchange: row k becomes the scaled pivot row, row p the old row k ----
 #pragma unroll
-            for (int q = 0; q < RPT; ++q)
+            for (int q = 0; q < RPT; ++q) {
                 if (tid == tk && q == qk)
 #pragma unroll
                     for (int c = 0; c < SW; ++c) v[q][c] = s_rowk[c];
+                else if (p != k && tid == tp && q == qp)
+#pragma unroll
+                    for (int c = 0; c < SW; ++c) v[q][c] = s_bufB[c];
+            }
             // ---- eliminate column k from every other row ----
 #pragma unroll
             for (int q = 0; q < RPT; ++q) {
@@ -655,15 +643,57 @@ __global__ void __launch_bounds__(512, 1) k_oz_subpanel_rows(int n, int k0, int 
         }
     }
     // ---- last sub-panel: the panel's exchanges on the columns outside it ----
-    for (int j = tid; j < n && sp == OZ_B / SW - 1; j += nt) {
-        if (j >= k0 && j < k0 + OZ_B) continue;
-        for (int kc = 0; kc < OZ_B; ++kc) {
-            const int k = k0 + kc, p = perm[k];
-            if (p != k) {
-                const double a = M[(long long)k * n + j];
-                M[(long long)k * n + j] = M[(long long)p * n + j];
-                M[(long long)p * n + j] = a;
+    // The 64 exchanges (k, perm[k]), applied in pivot order, compose into one
+    // permutation of at most 128 rows: row r receives the old row src[r].  It
+    // is built once in shared memory; then every 32-column tile of those rows
+    // is gathered into shared memory (independent, coalesced loads) and
+    // written back permuted, instead of 64 dependent swaps per column.
+    if (sp == OZ_B / SW - 1) {
+        __shared__ int s_src[2048];            // n <= 2048 for this kernel
+        __shared__ int s_from[2 * OZ_B], s_to[2 * OZ_B];
+        __shared__ int s_cnt;
+        __shared__ double s_xb[2 * OZ_B][33];
+        for (int r = tid; r < n; r += nt) s_src[r] = r;
+        if (tid == 0) s_cnt = 0;
+        __syncthreads();
+        if (tid == 0)
+            for (int kc = 0; kc < OZ_B; ++kc) {
+                const int k = k0 + kc, p = perm[k];
+                const int a = s_src[k];
+                s_src[k] = s_src[p];
+                s_src[p] = a;
             }
+        __syncthreads();
+        for (int r = tid; r < n; r += nt)
+            if (s_src[r] != r) {
+                const int e = atomicAdd(&s_cnt, 1);   // at most 2 * OZ_B rows move
+                s_to[e] = r;
+                s_from[e] = s_src[r];
+            }
+        __syncthreads();
+        const int cnt = s_cnt;
+        for (int j0 = 0; j0 < n && cnt > 0; j0 += 32) {
+            if (j0 >= k0 && j0 < k0 + OZ_B) continue;   // the panel's own columns (64-aligned)
+            // eight independent loads per thread in flight before any store
+            for (int e0 = tid; e0 < cnt * 32; e0 += 8 * nt) {
+                double x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * nt;
+                    x[u] = e < cnt * 32 ? M[(long long)s_from[e >> 5] * n + j0 + (e & 31)] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * nt;
+                    if (e < cnt * 32) s_xb[e >> 5][e & 31] = x[u];
+                }
+            }
+            __syncthreads();
+            for (int e = tid; e < cnt * 32; e += nt) {
+                const int q = e >> 5, jj = e & 31;
+                M[(long long)s_to[q] * n + j0 + jj] = s_xb[q][jj];
+            }
+            __syncthreads();
         }
     }
     if (tid == 0) Z.sing[w] = s_sing;
@@ -702,7 +732,8 @@ __global__ void __launch_bounds__(RT) k_oz_finish(int n, OzWork Z, DevState<doub
     }
     double la = 0.0;
     int neg = 0;
-    if (n <= 1024) {
+    const bool piv_rec = n <= OZ_SUBPANEL_MAX_N;   // the sub-panel path records the pivots
+    if (piv_rec) {
         // log|det| = sum log|pivot|, sign = prod sign(pivot) * (-1)^(row exchanges)
         const double* pv = Z.piv + (long long)w * n;
         for (int k = threadIdx.x; k < n; k += RT) {
@@ -719,8 +750,8 @@ __global__ void __launch_bounds__(RT) k_oz_finish(int n, OzWork Z, DevState<doub
     __syncthreads();
     if (threadIdx.x == 0) {
         const int sing = Z.sing[w];
-        const double lg = n <= 1024 ? la : Z.logacc[w];
-        const double sg = n <= 1024 ? (s_neg ? -1.0 : 1.0) : Z.sgnacc[w];
+        const double lg = piv_rec ? la : Z.logacc[w];
+        const double sg = piv_rec ? (s_neg ? -1.0 : 1.0) : Z.sgnacc[w];
         S.logabs[w] = sing ? -INFINITY : lg;
         S.sgn[w] = sing ? 0.0 : s_renorm(sg);
         if (delayed && reset_tau) S.tau[w] = 0;
@@ -772,13 +803,21 @@ void launch_oz_load(int W, int n, const double* A, double* M, const uint8_t* mas
     k_oz_load<<<dim3(n / 32, n / 32, W), dim3(32, 8), 0, st>>>(n, A, M, mask);
 }
 
+int oz_subpanel_width(int n) { return n <= 1024 ? 16 : 8; }
+
 bool launch_oz_subpanel(int W, int n, int k0, int sp, const OzWork& Z, const uint8_t* mask, cudaStream_t st) {
     if (n <= 512) {
-        k_oz_subpanel_rows<1><<<W, n, 0, st>>>(n, k0, sp, Z, mask);
+        k_oz_subpanel_rows<1, 16><<<W, n, 0, st>>>(n, k0, sp, Z, mask);
         return true;
     }
     if (n <= 1024) {
-        k_oz_subpanel_rows<2><<<W, n / 2, 0, st>>>(n, k0, sp, Z, mask);
+        k_oz_subpanel_rows<2, 16><<<W, n / 2, 0, st>>>(n, k0, sp, Z, mask);
+        return true;
+    }
+    if (n <= OZ_SUBPANEL_MAX_N && n % 4 == 0) {
+        // four rows of eight sub-panel columns per thread keep the registers
+        // of the 16-column form
+        k_oz_subpanel_rows<4, 8><<<W, n / 4, 0, st>>>(n, k0, sp, Z, mask);
         return true;
     }
     return false;

@@ -3,10 +3,10 @@
 // The refresh (Sec. 2.3 init_det_carrier; Sec. 1 advises double precision) is
 // a blocked Gauss-Jordan inversion of M = A^T, n^3 FMAs per walker, and
 // GB300's FP64 pipe runs at about 1/64 of its FP32 rate.  Panels of OZ_B = 64
-// columns are eliminated in four 16-column sub-panels: each in FP64
-// (refresh.cu: n * 16^2 FMAs), its update of the panel's other 48 columns as
-// the split product below with K = 16 (for n > 1024 the whole panel stays in
-// FP64); then the update of every other column by the panel,
+// columns are eliminated in four 16-column sub-panels (eight 8-column ones for
+// n > 1024): each in FP64 (refresh.cu: n * 16^2 FMAs), its update of the
+// panel's other columns as the split product below with one K-step of 16;
+// then the update of every other column by the panel,
 //     M[i, j] += sum_c (Pan - E)[i, c] * S[c, j],   S = rows k0 .. k0+63 of M,
 // (n^2 * 64 FMAs per panel: 94% of the work at n = 1024) also runs as an
 // error-free split product on the BF16 tensor cores, the scheme of Ozaki,
@@ -96,7 +96,9 @@ __device__ __forceinline__ void oz_digits(long long X, uint16_t (&h)[OZ_S]) {
 
 // Rows of (Pan - E): row i of walker w, the width (<= 64) columns c0 .. of M,
 // minus 1 at (c0 + c, c); columns past the width are zero.  One warp per row;
-// lane covers c = lane and lane + 32.
+// lane covers c = lane and lane + 32.  A width of at most 16 (a sub-panel)
+// feeds a single K-step of 16, which reads only the first 16 columns of each
+// slice row, so only those are written.
 __global__ void __launch_bounds__(256) k_oz_slice_P(int n, int c0, int width, int w0, OzWork Z,
                                                     const uint8_t* mask) {
     const int w = w0 + blockIdx.y;
@@ -113,18 +115,20 @@ __global__ void __launch_bounds__(256) k_oz_slice_P(int n, int c0, int width, in
     uint16_t ha[OZ_S], hb[OZ_S];
     oz_digits(oz_fixed(a, E), ha);
     oz_digits(oz_fixed(b, E), hb);
+    const bool full = width > 16;
 #pragma unroll
     for (int t = 0; t < OZ_S; ++t) {
         uint16_t* dst = Z.Pb + (((long long)w * OZ_S + t) * n + i) * OZ_B;
-        dst[lane] = ha[t];
-        dst[lane + 32] = hb[t];
+        if (full || lane < 16) dst[lane] = ha[t];
+        if (full) dst[lane + 32] = hb[t];
     }
     if (lane == 0) Z.eP[(long long)w * n + i] = E;
 }
 
 // Columns of S = the nr (<= 64) rows r0 .. of M, zero past nr: a 64 x 64
 // block per CTA (column blocks jb0, jb0 + 1, ..) through shared memory
-// (stored transposed), then one warp per column j.
+// (stored transposed), then one warp per column j.  As for the panel rows,
+// nr <= 16 writes only the first 16 entries of each slice row.
 __global__ void __launch_bounds__(256) k_oz_slice_S(int n, int r0, int nr, int jb0, int w0, OzWork Z,
                                                     const uint8_t* mask) {
     __shared__ double sT[64][65];   // sT[j][c] = S[c][j0 + j]
@@ -148,8 +152,8 @@ __global__ void __launch_bounds__(256) k_oz_slice_S(int n, int r0, int nr, int j
 #pragma unroll
         for (int t = 0; t < OZ_S; ++t) {
             uint16_t* dst = Z.Sb + (((long long)w * OZ_S + t) * n + j0 + j) * OZ_B;
-            dst[lane] = ha[t];
-            dst[lane + 32] = hb[t];
+            if (nr > 16 || lane < 16) dst[lane] = ha[t];
+            if (nr > 16) dst[lane + 32] = hb[t];
         }
         if (lane == 0) Z.eS[(long long)w * n + j0 + j] = E;
     }
@@ -478,12 +482,12 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     launch_oz_load(W, n, A, Z.M, mask, st);
-    constexpr int SW = 16;   // sub-panel width
+    const int SW = oz_subpanel_width(n);   // sub-panel width
     for (int k0 = 0; k0 < n; k0 += OZ_B) {
         if (hook) hook(hctx, 4, 1);
-        if (n <= 1024) {
+        if (n <= OZ_SUBPANEL_MAX_N) {
             // sub-panels: FP64 elimination, then the update of the other panel
-            // columns as a K = 16 split product on the panel's 128-column tile
+            // columns as a one-K-step split product on the panel's 128-column tile
             const int jt = k0 / OZ_TJ;
             for (int sp = 0; sp < OZ_B / SW; ++sp) {
                 const int ks = k0 + SW * sp;

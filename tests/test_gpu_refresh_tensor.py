@@ -21,10 +21,15 @@ def slater_batch(seed, W, n, var=None):
     return np.stack([Phi[o] for o in occ])
 
 
-@pytest.mark.parametrize("n", [128, 256, 384])
+@pytest.mark.parametrize("n", [128, 256, 384, 1152, 2048])
 def test_tensor_refresh_matches_oracle_and_fp64(n):
+    """n <= 1024: 16-column FP64 sub-panels; above: 8-column sub-panels with
+    four rows per thread (1152: an odd number, nine, of 128-column tiles;
+    2048 is the largest n).  At n = 2048 the oracle's pure-numpy LU takes
+    ~20 s a matrix, so it checks walker 0 there and the FP64 Gauss-Jordan
+    form checks every walker."""
     L = lrugb()
-    W = 5
+    W = 5 if n <= 1152 else 4
     A = slater_batch(810 + n, W, n)
     A[2] = A[2] * 1e3                   # scale spread between walkers
     A[3, :, 5] *= 1e-6                  # spread inside one matrix
@@ -36,12 +41,16 @@ def test_tensor_refresh_matches_oracle_and_fp64(n):
     la_tc, la_fp = la_tc.cpu().numpy(), la_fp.cpu().numpy()
     s_tc, s_fp = s_tc.cpu().numpy(), s_fp.cpu().numpy()
     for w in range(W):
+        assert fro_rel(inv_tc[w], inv_fp[w]) <= 1e-10, (w, fro_rel(inv_tc[w], inv_fp[w]))
+        assert abs(la_tc[w] - la_fp[w]) <= 1e-12 * max(1.0, abs(la_fp[w]))
+        assert s_tc[w] == s_fp[w]
+        if n > 1152 and w > 0:
+            continue
         ref = O.inv(A[w])
         sgn, la = O.slogdet(A[w])
         assert fro_rel(inv_tc[w], ref) <= 1e-10, (w, fro_rel(inv_tc[w], ref))
-        assert fro_rel(inv_tc[w], inv_fp[w]) <= 1e-10
         assert abs(la_tc[w] - la) <= 1e-12 * max(1.0, abs(la))
-        assert s_tc[w] == sgn == s_fp[w]
+        assert s_tc[w] == sgn
     tc.check_device_error()
 
 
