@@ -90,7 +90,12 @@ typedef enum {
     LRU_ARITH_NATIVE = 0,   /* FP64 FMAs */
     LRU_ARITH_DF = 1        /* double-float (pairs of FP32) from integer-split FP64 data, about 2^7 x
                                FP64's rounding: the delayed GEMV of rank-1 determinant updates
-                               (HBM-bound instead of FP64-bound) and the Pfaffian propose's pass */
+                               (HBM-bound instead of FP64-bound) and the Pfaffian propose's pass.
+                               For uniform-n Pfaffian handles that pass reads the inverse as exactly
+                               skew ((A^-1)_jl = -(A^-1)_lj, rows streamed contiguously), which the
+                               init, refresh, lru_accept and every flush keep bit for bit; after
+                               lru_step_persistent's plain Pfaffian accept (a generic Woodbury
+                               update, not exactly skew) refresh before such a propose */
 } lru_arith;
 
 /* How init and refresh compute the FP64 inverse (F64 determinant handles):
