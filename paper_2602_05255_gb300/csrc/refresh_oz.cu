@@ -125,6 +125,33 @@ __global__ void __launch_bounds__(256) k_oz_slice_P(int n, int c0, int width, in
     if (lane == 0) Z.eP[(long long)w * n + i] = E;
 }
 
+// The same rows for a sub-panel (width <= 16): half a warp per row, lane c of
+// the half covering column c, so no lane splits a zero.  Writes the first 16
+// entries of each slice row and the row's exponent, exactly as k_oz_slice_P.
+// n is a multiple of 16, so both halves of a warp always have a row.
+__global__ void __launch_bounds__(256) k_oz_slice_P16(int n, int c0, int width, int w0, OzWork Z,
+                                                      const uint8_t* mask) {
+    const int w = w0 + blockIdx.y;
+    if (mask && !mask[w]) return;
+    const int c = threadIdx.x & 15;
+    const int i = blockIdx.x * 16 + (threadIdx.x >> 4);
+    const unsigned hmask = 0xFFFFu << (threadIdx.x & 16);   // this half of the warp
+    const bool ok = i < n;
+    const double* row = Z.M + (long long)w * n * n + (long long)i * n + c0;
+    double a = (ok && c < width) ? row[c] : 0.0;
+    if (c < width && i == c0 + c) a -= 1.0;
+    int mx = oz_bexp(a);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(hmask, mx, o));
+    const int E = mx > 0 ? mx - 1022 : 0;
+    uint16_t ha[OZ_S];
+    oz_digits(oz_fixed(a, E), ha);
+    if (!ok) return;
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) Z.Pb[(((long long)w * OZ_S + t) * n + i) * OZ_B + c] = ha[t];
+    if (c == 0) Z.eP[(long long)w * n + i] = E;
+}
+
 // Columns of S = the nr (<= 64) rows r0 .. of M, zero past nr: a 64 x 64
 // block per CTA (column blocks jb0, jb0 + 1, ..) through shared memory
 // (stored transposed), then one warp per column j.  As for the panel rows,
@@ -492,7 +519,7 @@ bool launch_refresh_oz(int W, int n, const double* A, const OzWork& Z, const Dev
             for (int sp = 0; sp < OZ_B / SW; ++sp) {
                 const int ks = k0 + SW * sp;
                 launch_oz_subpanel(W, n, k0, sp, Z, mask, st);
-                k_oz_slice_P<<<dim3(n / 8, W), 256, 0, st>>>(n, ks, SW, 0, Z, mask);
+                k_oz_slice_P16<<<dim3(n / 16, W), 256, 0, st>>>(n, ks, SW, 0, Z, mask);
                 k_oz_slice_S<<<dim3(OZ_TJ / 64, W), 256, 0, st>>>(n, ks, SW, jt * (OZ_TJ / 64), 0, Z, mask);
                 const OzCols inner{k0, k0 + OZ_B, ks, ks + SW, jt, jt + 1};
                 k_oz_gemm<1><<<nsm, OZ_THREADS, dyn, st>>>(maps, W, 0, n, inner, Z, mask, err);
