@@ -319,6 +319,13 @@ def flop_factor(cfg):
 # --------------------------------------------------------------------------
 # timing
 # --------------------------------------------------------------------------
+def refresh_share(steps, every):
+    """The part of one refresh that `steps` steps owe the schedule beyond the
+    refreshes due inside them: steps/every - floor(steps/every) (0 without a
+    refresh period)."""
+    return (steps / every - steps // every) if every else 0.0
+
+
 def timed_steps(torch, st, step, args, dist, dev, refresh=None, every=0):
     """W warm-up steps, then K steps between CUDA events on the launching
     stream (barrier + synchronize on both sides, clocks sampled meanwhile,
@@ -356,7 +363,7 @@ def timed_steps(torch, st, step, args, dist, dev, refresh=None, every=0):
     st.profile(False)
     ms = multigpu.max_over_ranks(ms, dist, "cuda")
     amort = None
-    frac = (args.steps / every - args.steps // every) if (every and refresh) else 0.0
+    frac = refresh_share(args.steps, every) if refresh else 0.0
     if frac > 0:
         if dist:
             dist.barrier()
@@ -787,7 +794,7 @@ def e2e_det(L, torch, cfg, K, arm, Phi_d, occ0, slot_h, new_h, steps):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    frac = (steps / every - steps // every) if every else 0.0
+    frac = refresh_share(steps, every)
     added = 0.0
     if frac > 0:
         # the schedule's refresh share the steps did not reach, as in the device-timed arm

@@ -93,3 +93,13 @@ def test_drift_vs_plain_gates_near_nodes():
     assert d["near_node_steps"] == 1
     assert math.isclose(d["max_rel"], 1e-8, rel_tol=1e-6)
     assert "ratio_err_vs_plain_fp64" not in arms["plain"]
+
+
+def test_refresh_share_of_a_short_window():
+    # 20 steps of a schedule that refreshes every 128 steps owe 20/128 of a
+    # refresh; 256 steps hold both refreshes themselves; 300 steps hold two and
+    # owe 44/128 of a third; no period, no share
+    assert math.isclose(bench.refresh_share(20, 128), 20 / 128)
+    assert bench.refresh_share(256, 128) == 0.0
+    assert math.isclose(bench.refresh_share(300, 128), 44 / 128)
+    assert bench.refresh_share(64, 0) == 0.0
